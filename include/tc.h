@@ -1,0 +1,214 @@
+/*
+ * tc.h — C ABI of the GB300 cover-edge triangle-counting library (libcetc).
+ *
+ * Method: D. A. Bader et al., "Triangle Counting Through Cover-Edges"
+ * (arXiv 2210.00389).  Alg. 1 (CETC): label every vertex with its BFS level
+ * (Def. 2), take the horizontal edges (both ends on one level) as the
+ * cover-edge set H (Thm. 1), and for every (u,v) in H with u < v count the
+ * common neighbours w with L(w) != L(u), or L(w) = L(u) and w > v (Thm. 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: TC_OK (0) or a negative TC_ERR_* code.  No C++ exception
+ *    ever crosses this boundary.  tc_strerror() names a code;
+ *    tc_last_error() gives a message for the calling thread's last failure.
+ *  - Graphs are simple and undirected, given as a symmetric CSR (Sec. III-B):
+ *    offsets int64[n+1] (offsets[0] = 0, non-decreasing, offsets[n] = nnz),
+ *    cols uint32[nnz], every row sorted strictly ascending, no self-loops,
+ *    every entry < n.  nnz = 2|E|.
+ *  - "host or device" pointers are classified with cudaPointerGetAttributes:
+ *    device (or managed) memory of the current device is written/read on
+ *    the GPU, anything else is treated as host memory.
+ *  - Every call on a tc_graph runs on the CUDA stream given at creation and
+ *    returns only after its results are complete and visible to the host.
+ *  - A tc_graph may be used by one thread at a time; different graphs and
+ *    servers are independent.
+ *  - Device faults are never raised on purpose: device-side checks set an
+ *    error word that the host turns into a status code.
+ */
+#ifndef TC_H_
+#define TC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = -1,   /* NULL where a pointer is required, bad mode, ... */
+  TC_ERR_INVALID_GRAPH = -2, /* CSR breaks the rules above (validation flags)   */
+  TC_ERR_OOM = -3,           /* device allocation failed / over budget          */
+  TC_ERR_CUDA = -4,          /* a CUDA runtime call failed                      */
+  TC_ERR_CAPACITY = -5,      /* caller's output buffer too small                */
+  TC_ERR_TIMEOUT = -6,       /* a bounded device/host wait ran out              */
+  TC_ERR_AGAIN = -7,         /* queue full, try later                           */
+  TC_ERR_NOT_FOUND = -8,     /* unknown ticket / graph id                       */
+  TC_ERR_CANCELLED = -9      /* request cancelled (server shut down)            */
+};
+
+/* Static string naming a status code (never NULL). */
+const char* tc_strerror(int status);
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* tc_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int tc_version(void);
+
+/* --------------------------------------------------------------- memory */
+/* Route the library's device allocations (graph buffers and temporaries)
+ * through caller callbacks, e.g. a framework's caching allocator.
+ * alloc(bytes, stream, ctx) returns device memory usable on `stream` or NULL;
+ * free(ptr, stream, ctx) releases it.  Pass NULLs to restore the default
+ * (cudaMallocAsync / cudaFreeAsync on the call's stream).  Process-wide; call
+ * it while no graph or server exists.  Returns TC_ERR_INVALID_ARG when only
+ * one of the two callbacks is given. */
+typedef void* (*tc_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*tc_free_fn)(void* ptr, void* stream, void* ctx);
+int tc_set_allocator(tc_alloc_fn alloc, tc_free_fn free_fn, void* ctx);
+
+/* ---------------------------------------------------------------- graphs */
+typedef struct tc_graph tc_graph; /* opaque: device CSR + cached levels and H */
+
+/* Borrowed view of a caller-owned CSR; read only during the call unless
+ * TC_GRAPH_BORROW is given. */
+typedef struct {
+  const int64_t* offsets; /* int64[n+1] */
+  const uint32_t* cols;   /* uint32[nnz] */
+  uint32_t n;             /* |V| */
+  int64_t nnz;            /* 2|E| = offsets[n] */
+  int on_device;          /* 0: host pointers, 1: device pointers */
+} tc_csr_view;
+
+enum {
+  TC_GRAPH_VALIDATE = 1u,   /* check the CSR rules on the GPU (O(n + nnz))   */
+  TC_GRAPH_CHECK_SYM = 2u,  /* also check symmetry: (u,v) present => (v,u)   */
+  TC_GRAPH_BORROW = 4u      /* device views only: keep using the caller's
+                               buffers instead of copying; they must stay
+                               alive and unchanged until tc_graph_destroy    */
+};
+
+/* Build a graph object from a CSR (Sec. III-B input format).  Host views are
+ * copied to the device; device views are copied device-to-device unless
+ * TC_GRAPH_BORROW.  Also computes the degree of every vertex.  Errors:
+ * TC_ERR_INVALID_ARG (NULL csr/out, nnz < 0, BORROW on a host view),
+ * TC_ERR_INVALID_GRAPH (validation failed; *out untouched), TC_ERR_OOM,
+ * TC_ERR_CUDA.  `cuda_stream` may be NULL (the legacy default stream). */
+int tc_graph_create(const tc_csr_view* csr, uint32_t flags, void* cuda_stream,
+                    tc_graph** out);
+/* Release every device buffer the graph owns.  NULL is a no-op. */
+int tc_graph_destroy(tc_graph* g);
+/* Drop cached levels, cover edges and counts so the next call recomputes
+ * them (used to time the full path). */
+int tc_graph_invalidate(tc_graph* g);
+
+typedef struct {
+  uint32_t n;
+  int64_t nnz;          /* 2|E| */
+  int64_t num_edges;    /* |E| */
+  uint32_t max_degree;
+  int64_t nlevels;      /* 1 + max level, or -1 if levels are not computed */
+  int64_t num_cover;    /* |H|, or -1 if not computed */
+  uint32_t num_roots;   /* BFS roots of the last level computation */
+} tc_graph_info_t;
+int tc_graph_info(const tc_graph* g, tc_graph_info_t* info);
+
+/* Def. 2 and Alg. 1 lines 2-3: BFS levels, L(v) = shortest distance from
+ * the root of v's connected component.
+ *   roots == NULL (nroots ignored): the first root is the vertex of maximum
+ *     degree (lowest id on ties); every other component is rooted at its
+ *     lowest vertex id.
+ *   roots != NULL: host array of nroots vertex ids, taken in order; a root
+ *     in a component already reached by an earlier root is skipped; every
+ *     component no root reaches is rooted at its lowest id.
+ * levels_out: NULL, or host/device uint32[n] receiving L.  nlevels_out: NULL
+ * or receives 1 + max L (0 when n = 0).  Levels are cached in the graph (and
+ * any cached cover-edge set is dropped).  Errors: TC_ERR_INVALID_ARG (root
+ * >= n), TC_ERR_OOM, TC_ERR_CUDA. */
+int tc_bfs_levels(tc_graph* g, const uint32_t* roots, uint32_t nroots,
+                  uint32_t* levels_out, uint32_t* nlevels_out);
+
+/* Thm. 1 and Alg. 1 lines 4-5: the cover-edge set
+ * H = {(u,v) in E : u < v, L(u) = L(v)} in ascending (u, v) order (CSR
+ * order).  Computes levels with the default root rule if none are cached.
+ * uv_out: NULL or host/device uint32[2*cap], pair i = (uv[2i], uv[2i+1]).
+ * *count_out receives |H|.  If |H| > cap and uv_out != NULL, nothing is
+ * written to uv_out and TC_ERR_CAPACITY is returned (with *count_out set). */
+int tc_cover_edges(tc_graph* g, uint32_t* uv_out, int64_t cap, int64_t* count_out);
+
+enum {
+  TC_MODE_COVER = 0, /* Alg. 1: cover edges + count-once rule (Thm. 2)       */
+  TC_MODE_PLAIN = 1  /* direction-oriented edge iterator over every edge
+                        u < v, counting common neighbours w > v (Sec. I, V-A) */
+};
+
+/* Exact triangle count T (uint64, host pointer count_out).  TC_MODE_COVER
+ * runs BFS + cover extraction if not cached, then the intersection with the
+ * count-once rule and the reduction; TC_MODE_PLAIN runs the intersection
+ * over every edge.  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA. */
+int tc_count(tc_graph* g, int mode, uint64_t* count_out);
+
+/* Per-cover-edge counts of Alg. 1 line 7: counts_out[i] = number of w that
+ * the count-once rule accepts for cover edge i (in tc_cover_edges order).
+ * counts_out: host/device uint32[cap].  TC_ERR_CAPACITY if |H| > cap. */
+int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap);
+
+/* Timings (device ms, CUDA events on the graph's stream) of the most recent
+ * tc_count / tc_bfs_levels / tc_cover_edges call, per stage, and work sizes. */
+typedef struct {
+  float ms_validate, ms_bfs, ms_cover, ms_bucket, ms_intersect, ms_total;
+  uint32_t bfs_levels;        /* level-synchronous iterations run */
+  uint32_t bfs_bottom_up;     /* of which bottom-up */
+  int64_t edges_intersected;  /* |H| (cover) or |E| (plain) */
+  int64_t list_elems;         /* sum of list lengths handed to the intersection */
+  uint64_t matches;           /* common neighbours found before the predicate */
+} tc_stats_t;
+int tc_graph_stats(const tc_graph* g, tc_stats_t* out);
+
+/* ---------------------------------------------------------------- batch */
+/* Tunables of the intersection (NULL anywhere = built-in / autotuned). */
+typedef struct {
+  int32_t small_max;       /* longer list <= small_max: sub-warp merge bucket */
+  int32_t hub_min;         /* owner degree >= hub_min: hub (shared-memory) bucket */
+  int32_t block_threads;   /* threads per block of the persistent batch kernel */
+  int32_t blocks_per_sm;   /* resident blocks per SM of the persistent kernel */
+  int32_t reserved[4];
+} tc_options;
+
+/* Count ngraphs independent graphs in one persistent, CUDA-graph-captured
+ * launch sequence.  graphs: host array of views (host or device pointers).
+ * counts_out: host uint64[ngraphs]; status_out: host int[ngraphs] (NULL
+ * allowed) with a per-graph status (TC_OK or TC_ERR_INVALID_GRAPH).
+ * Returns TC_OK if the batch ran (per-graph failures are in status_out). */
+int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mode,
+                   const tc_options* opt, void* cuda_stream, uint64_t* counts_out,
+                   int* status_out);
+
+/* ---------------------------------------------------------------- serving */
+typedef struct tc_server tc_server;
+typedef struct {
+  size_t hbm_budget_bytes; /* admission limit for resident + in-flight graphs */
+  int32_t slots;           /* max requests in flight on the device */
+  int32_t queue_capacity;  /* max queued (not yet admitted) requests */
+  int32_t wait_limit_ms;   /* bound on any internal wait (0 = 10000) */
+  int32_t reserved[4];
+} tc_serve_config;
+
+int tc_serve_create(const tc_serve_config* cfg, tc_server** out);
+/* Upload a graph that stays resident (CSR + levels + cover edges cached);
+ * *graph_id names it in later submits. */
+int tc_serve_register(tc_server* s, const tc_csr_view* csr, uint64_t* graph_id);
+/* Queue a count request: either a resident graph (csr_or_null == NULL) or a
+ * one-shot CSR (copied before return).  TC_ERR_AGAIN when the queue is full. */
+int tc_serve_submit(tc_server* s, const tc_csr_view* csr_or_null, uint64_t graph_id,
+                    int mode, uint64_t* ticket);
+/* Non-blocking: *done = 1 when the request finished, with its count and status. */
+int tc_serve_poll(tc_server* s, uint64_t ticket, int* done, uint64_t* count, int* status);
+int tc_serve_destroy(tc_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H_ */

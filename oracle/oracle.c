@@ -1,0 +1,217 @@
+/*
+ * CPU ORACLE for cover-edge triangle counting (CETC).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously-correct
+ * definition that the CUDA path is checked against.  Only the test suite,
+ * the package's smoke check and the benchmark's CPU-baseline leg may load
+ * it; the library's product path never calls it and shares no code with it
+ * (no headers, helpers, tables or pre/post-processing in common).
+ *
+ * Source: D. A. Bader et al., "Triangle Counting Through Cover-Edges"
+ * (arXiv 2210.00389).  Every function below cites the passage it follows.
+ *
+ * Input everywhere: a simple undirected graph as a symmetric CSR
+ * (Sec. III-B: "The input graph G is stored in a compressed sparse row (CSR)
+ * format"): off[n+1] (int64), cols[off[n]] (uint32), each row sorted
+ * ascending with no duplicates and no self-loops.
+ *
+ * Readings of the paper taken here (the paper is silent on them):
+ *   - Root rule.  Alg. 1 starts a BFS "from any unvisited vertex".  The first
+ *     root is the vertex of maximum degree (lowest id on ties); after its
+ *     component, vertices are scanned in ascending id order and every still
+ *     unvisited one starts a new BFS, i.e. every other component is rooted
+ *     at its lowest id.  A caller may instead pass an explicit root list,
+ *     used in order (a root already reached is skipped) before the scan.
+ *   - Levels are BFS distances from the component root (Def. 2), so they do
+ *     not depend on the traversal order, only on the roots.
+ *   - Counts are exact unsigned 64-bit integers.
+ *
+ * Parity status: every function here is pinned by tests that do not call
+ * it to compute their expected value (brute force, trace(A^3)/6, library
+ * BFS distances, closed forms, Lemma 1 / Lemma 2 invariants).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_EXPORT __attribute__((visibility("default")))
+#define OR_UNVISITED 0xFFFFFFFFu
+
+/* ------------------------------------------------------------------------ */
+/* Def. 2 + Alg. 1 (lines 2-3): BFS levels, restarted from every unvisited
+ * vertex.  L[v] = shortest distance from the root of v's component.
+ * Returns the number of levels (1 + max L), 0 for n = 0, -1 on bad input. */
+static void bfs_from(uint32_t root, const int64_t* off, const uint32_t* cols,
+                     uint32_t* L, uint32_t* queue) {
+  int64_t head = 0, tail = 0;
+  L[root] = 0;
+  queue[tail++] = root;
+  while (head < tail) {
+    uint32_t x = queue[head++];
+    for (int64_t e = off[x]; e < off[x + 1]; ++e) {
+      uint32_t y = cols[e];
+      if (L[y] == OR_UNVISITED) {
+        L[y] = L[x] + 1;
+        queue[tail++] = y;
+      }
+    }
+  }
+}
+
+OR_EXPORT int64_t or_bfs_levels(uint32_t n, const int64_t* off, const uint32_t* cols,
+                                const uint32_t* roots, uint32_t nroots, uint32_t* L) {
+  if (n == 0) return 0;
+  uint32_t* queue = (uint32_t*)malloc(sizeof(uint32_t) * n);
+  if (!queue) return -1;
+  for (uint32_t v = 0; v < n; ++v) L[v] = OR_UNVISITED;
+
+  if (roots && nroots > 0) {
+    for (uint32_t i = 0; i < nroots; ++i) {
+      if (roots[i] >= n) { free(queue); return -1; }
+      if (L[roots[i]] == OR_UNVISITED) bfs_from(roots[i], off, cols, L, queue);
+    }
+  } else {
+    /* first root: maximum degree, lowest id on ties */
+    uint32_t r0 = 0;
+    for (uint32_t v = 1; v < n; ++v)
+      if (off[v + 1] - off[v] > off[r0 + 1] - off[r0]) r0 = v;
+    bfs_from(r0, off, cols, L, queue);
+  }
+  /* Alg. 1 line 2-3: every vertex still unvisited starts its own BFS */
+  for (uint32_t v = 0; v < n; ++v)
+    if (L[v] == OR_UNVISITED) bfs_from(v, off, cols, L, queue);
+
+  uint32_t maxL = 0;
+  for (uint32_t v = 0; v < n; ++v) if (L[v] > maxL) maxL = L[v];
+  free(queue);
+  return (int64_t)maxL + 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thm. 1 + Alg. 1 (lines 4-5): the cover-edge set H = horizontal edges,
+ * {(u,v) in E : L(u) = L(v), u < v}, emitted in ascending (u, v) order.
+ * A tree edge always joins adjacent levels, so "non-tree edge with both ends
+ * on one level" (Def. 2) is exactly "both ends on one level".
+ * Writes at most cap pairs (uv[2i] = u, uv[2i+1] = v); returns |H|. */
+OR_EXPORT int64_t or_cover_edges(uint32_t n, const int64_t* off, const uint32_t* cols,
+                                 const uint32_t* L, uint32_t* uv, int64_t cap) {
+  int64_t h = 0;
+  for (uint32_t u = 0; u < n; ++u) {
+    for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = cols[e];
+      if (u < v && L[u] == L[v]) {
+        if (uv && h < cap) { uv[2 * h] = u; uv[2 * h + 1] = v; }
+        ++h;
+      }
+    }
+  }
+  return h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 1 (lines 6-8) for one cover edge (u, v), u < v, L(u) = L(v):
+ * the number of w in N(u) ∩ N(v) with L(u) != L(w), or L(u) = L(w) and
+ * v < w.  N(u) ∩ N(v) is found by the two-pointer merge of the two sorted
+ * adjacency lists (merge-path intersection, Sec. V-A). */
+static uint64_t cover_edge_count(const int64_t* off, const uint32_t* cols,
+                                 const uint32_t* L, uint32_t u, uint32_t v) {
+  uint64_t c = 0;
+  int64_t i = off[u], iend = off[u + 1];
+  int64_t j = off[v], jend = off[v + 1];
+  while (i < iend && j < jend) {
+    uint32_t a = cols[i], b = cols[j];
+    if (a < b) {
+      ++i;
+    } else if (b < a) {
+      ++j;
+    } else {
+      uint32_t w = a;
+      if (L[u] != L[w] || (L[u] == L[w] && v < w)) ++c;
+      ++i; ++j;
+    }
+  }
+  return c;
+}
+
+/* Alg. 1 in full after the BFS: T = sum over cover edges of the count above. */
+OR_EXPORT uint64_t or_cetc_count(uint32_t n, const int64_t* off, const uint32_t* cols,
+                                 const uint32_t* L) {
+  uint64_t T = 0;
+  for (uint32_t u = 0; u < n; ++u) {
+    for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = cols[e];
+      if (L[u] == L[v] && u < v) T += cover_edge_count(off, cols, L, u, v);
+    }
+  }
+  return T;
+}
+
+/* Per-edge counts of Alg. 1 line 7 for an explicit list of k cover edges
+ * (uv[2i], uv[2i+1]).  Returns -1 if an entry is not a cover edge (u >= v,
+ * levels differ or (u, v) not in E), else 0. */
+OR_EXPORT int or_cetc_edge_counts(uint32_t n, const int64_t* off, const uint32_t* cols,
+                                  const uint32_t* L, const uint32_t* uv, int64_t k,
+                                  uint32_t* counts) {
+  for (int64_t i = 0; i < k; ++i) {
+    uint32_t u = uv[2 * i], v = uv[2 * i + 1];
+    if (u >= n || v >= n || !(u < v) || L[u] != L[v]) return -1;
+    int found = 0;
+    for (int64_t e = off[u]; e < off[u + 1]; ++e) if (cols[e] == v) { found = 1; break; }
+    if (!found) return -1;
+    counts[i] = (uint32_t)cover_edge_count(off, cols, L, u, v);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The plain direction-oriented edge iterator (Sec. I and Sec. V-A): every
+ * edge u < v, every common neighbour w > v, so each triangle a < b < c is
+ * counted once, at its edge (a, b) with apex c. */
+OR_EXPORT uint64_t or_plain_count(uint32_t n, const int64_t* off, const uint32_t* cols) {
+  uint64_t T = 0;
+  for (uint32_t u = 0; u < n; ++u) {
+    for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = cols[e];
+      if (!(u < v)) continue;
+      int64_t i = off[u], iend = off[u + 1];
+      int64_t j = off[v], jend = off[v + 1];
+      while (i < iend && j < jend) {
+        uint32_t a = cols[i], b = cols[j];
+        if (a < b) ++i;
+        else if (b < a) ++j;
+        else { if (a > v) ++T; ++i; ++j; }
+      }
+    }
+  }
+  return T;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Triangle finding (abstract; Sec. VI): every triangle {a < b < c} listed
+ * once, in ascending (a, b, c) order.  Writes at most cap triples; returns
+ * the number of triangles. */
+OR_EXPORT int64_t or_triangles(uint32_t n, const int64_t* off, const uint32_t* cols,
+                               uint32_t* abc, int64_t cap) {
+  int64_t t = 0;
+  for (uint32_t a = 0; a < n; ++a) {
+    for (int64_t e = off[a]; e < off[a + 1]; ++e) {
+      uint32_t b = cols[e];
+      if (b <= a) continue;
+      int64_t i = off[a], iend = off[a + 1];
+      int64_t j = off[b], jend = off[b + 1];
+      while (i < iend && j < jend) {
+        uint32_t x = cols[i], y = cols[j];
+        if (x < y) ++i;
+        else if (y < x) ++j;
+        else {
+          if (x > b) {
+            if (abc && t < cap) { abc[3 * t] = a; abc[3 * t + 1] = b; abc[3 * t + 2] = x; }
+            ++t;
+          }
+          ++i; ++j;
+        }
+      }
+    }
+  }
+  return t;
+}

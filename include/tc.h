@@ -12,7 +12,7 @@
  *  - Return value: TC_OK (0) or a negative TC_ERR_* code.  No C++ exception
  *    ever crosses this boundary.  tc_strerror() names a code;
  *    tc_last_error() gives a message for the calling thread's last failure.
- *  - Graphs are simple and undirected, given as a symmetric CSR (Sec. III-B):
+ *  - Graphs are simple and undirected, given as a symmetric CSR (the input format of Sec. III):
  *    offsets int64[n+1] (offsets[0] = 0, non-decreasing, offsets[n] = nnz),
  *    cols uint32[nnz], every row sorted strictly ascending, no self-loops,
  *    every entry < n.  nnz = 2|E|.
@@ -31,6 +31,12 @@
 
 #include <stddef.h>
 #include <stdint.h>
+
+#if defined(__GNUC__)
+#define TC_API __attribute__((visibility("default")))
+#else
+#define TC_API
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -51,11 +57,14 @@ enum {
 };
 
 /* Static string naming a status code (never NULL). */
-const char* tc_strerror(int status);
+TC_API const char* tc_strerror(int status);
 /* Message describing the calling thread's most recent failure ("" if none). */
-const char* tc_last_error(void);
+TC_API const char* tc_last_error(void);
 /* Library version, major*10000 + minor*100 + patch. */
-int tc_version(void);
+TC_API int tc_version(void);
+/* Diagnostics: number of CUDA kernels this library has launched in the
+ * process so far (all threads, all devices). */
+TC_API uint64_t tc_kernel_launches(void);
 
 /* --------------------------------------------------------------- memory */
 /* Route the library's device allocations (graph buffers and temporaries)
@@ -67,7 +76,7 @@ int tc_version(void);
  * one of the two callbacks is given. */
 typedef void* (*tc_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*tc_free_fn)(void* ptr, void* stream, void* ctx);
-int tc_set_allocator(tc_alloc_fn alloc, tc_free_fn free_fn, void* ctx);
+TC_API int tc_set_allocator(tc_alloc_fn alloc, tc_free_fn free_fn, void* ctx);
 
 /* ---------------------------------------------------------------- graphs */
 typedef struct tc_graph tc_graph; /* opaque: device CSR + cached levels and H */
@@ -90,19 +99,19 @@ enum {
                                alive and unchanged until tc_graph_destroy    */
 };
 
-/* Build a graph object from a CSR (Sec. III-B input format).  Host views are
+/* Build a graph object from a CSR (the input format of Sec. III).  Host views are
  * copied to the device; device views are copied device-to-device unless
  * TC_GRAPH_BORROW.  Also computes the degree of every vertex.  Errors:
  * TC_ERR_INVALID_ARG (NULL csr/out, nnz < 0, BORROW on a host view),
  * TC_ERR_INVALID_GRAPH (validation failed; *out untouched), TC_ERR_OOM,
  * TC_ERR_CUDA.  `cuda_stream` may be NULL (the legacy default stream). */
-int tc_graph_create(const tc_csr_view* csr, uint32_t flags, void* cuda_stream,
+TC_API int tc_graph_create(const tc_csr_view* csr, uint32_t flags, void* cuda_stream,
                     tc_graph** out);
 /* Release every device buffer the graph owns.  NULL is a no-op. */
-int tc_graph_destroy(tc_graph* g);
+TC_API int tc_graph_destroy(tc_graph* g);
 /* Drop cached levels, cover edges and counts so the next call recomputes
  * them (used to time the full path). */
-int tc_graph_invalidate(tc_graph* g);
+TC_API int tc_graph_invalidate(tc_graph* g);
 
 typedef struct {
   uint32_t n;
@@ -113,9 +122,9 @@ typedef struct {
   int64_t num_cover;    /* |H|, or -1 if not computed */
   uint32_t num_roots;   /* BFS roots of the last level computation */
 } tc_graph_info_t;
-int tc_graph_info(const tc_graph* g, tc_graph_info_t* info);
+TC_API int tc_graph_info(const tc_graph* g, tc_graph_info_t* info);
 
-/* Def. 2 and Alg. 1 lines 2-3: BFS levels, L(v) = shortest distance from
+/* Def. 2 and Alg. 1: BFS levels, L(v) = shortest distance from
  * the root of v's connected component.
  *   roots == NULL (nroots ignored): the first root is the vertex of maximum
  *     degree (lowest id on ties); every other component is rooted at its
@@ -127,16 +136,16 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info);
  * or receives 1 + max L (0 when n = 0).  Levels are cached in the graph (and
  * any cached cover-edge set is dropped).  Errors: TC_ERR_INVALID_ARG (root
  * >= n), TC_ERR_OOM, TC_ERR_CUDA. */
-int tc_bfs_levels(tc_graph* g, const uint32_t* roots, uint32_t nroots,
+TC_API int tc_bfs_levels(tc_graph* g, const uint32_t* roots, uint32_t nroots,
                   uint32_t* levels_out, uint32_t* nlevels_out);
 
-/* Thm. 1 and Alg. 1 lines 4-5: the cover-edge set
+/* Thm. 1 and Alg. 1: the cover-edge set
  * H = {(u,v) in E : u < v, L(u) = L(v)} in ascending (u, v) order (CSR
  * order).  Computes levels with the default root rule if none are cached.
  * uv_out: NULL or host/device uint32[2*cap], pair i = (uv[2i], uv[2i+1]).
  * *count_out receives |H|.  If |H| > cap and uv_out != NULL, nothing is
  * written to uv_out and TC_ERR_CAPACITY is returned (with *count_out set). */
-int tc_cover_edges(tc_graph* g, uint32_t* uv_out, int64_t cap, int64_t* count_out);
+TC_API int tc_cover_edges(tc_graph* g, uint32_t* uv_out, int64_t cap, int64_t* count_out);
 
 enum {
   TC_MODE_COVER = 0, /* Alg. 1: cover edges + count-once rule (Thm. 2)       */
@@ -148,12 +157,12 @@ enum {
  * runs BFS + cover extraction if not cached, then the intersection with the
  * count-once rule and the reduction; TC_MODE_PLAIN runs the intersection
  * over every edge.  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA. */
-int tc_count(tc_graph* g, int mode, uint64_t* count_out);
+TC_API int tc_count(tc_graph* g, int mode, uint64_t* count_out);
 
-/* Per-cover-edge counts of Alg. 1 line 7: counts_out[i] = number of w that
+/* Per-cover-edge counts of Alg. 1: counts_out[i] = number of w that
  * the count-once rule accepts for cover edge i (in tc_cover_edges order).
  * counts_out: host/device uint32[cap].  TC_ERR_CAPACITY if |H| > cap. */
-int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap);
+TC_API int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap);
 
 /* Timings (device ms, CUDA events on the graph's stream) of the most recent
  * tc_count / tc_bfs_levels / tc_cover_edges call, per stage, and work sizes. */
@@ -164,8 +173,9 @@ typedef struct {
   int64_t edges_intersected;  /* |H| (cover) or |E| (plain) */
   int64_t list_elems;         /* sum of list lengths handed to the intersection */
   uint64_t matches;           /* common neighbours found before the predicate */
+  uint32_t kernel_launches;   /* kernels launched by the call */
 } tc_stats_t;
-int tc_graph_stats(const tc_graph* g, tc_stats_t* out);
+TC_API int tc_graph_stats(const tc_graph* g, tc_stats_t* out);
 
 /* ---------------------------------------------------------------- batch */
 /* Tunables of the intersection (NULL anywhere = built-in / autotuned). */
@@ -182,7 +192,7 @@ typedef struct {
  * counts_out: host uint64[ngraphs]; status_out: host int[ngraphs] (NULL
  * allowed) with a per-graph status (TC_OK or TC_ERR_INVALID_GRAPH).
  * Returns TC_OK if the batch ran (per-graph failures are in status_out). */
-int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mode,
+TC_API int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mode,
                    const tc_options* opt, void* cuda_stream, uint64_t* counts_out,
                    int* status_out);
 
@@ -196,17 +206,17 @@ typedef struct {
   int32_t reserved[4];
 } tc_serve_config;
 
-int tc_serve_create(const tc_serve_config* cfg, tc_server** out);
+TC_API int tc_serve_create(const tc_serve_config* cfg, tc_server** out);
 /* Upload a graph that stays resident (CSR + levels + cover edges cached);
  * *graph_id names it in later submits. */
-int tc_serve_register(tc_server* s, const tc_csr_view* csr, uint64_t* graph_id);
+TC_API int tc_serve_register(tc_server* s, const tc_csr_view* csr, uint64_t* graph_id);
 /* Queue a count request: either a resident graph (csr_or_null == NULL) or a
  * one-shot CSR (copied before return).  TC_ERR_AGAIN when the queue is full. */
-int tc_serve_submit(tc_server* s, const tc_csr_view* csr_or_null, uint64_t graph_id,
+TC_API int tc_serve_submit(tc_server* s, const tc_csr_view* csr_or_null, uint64_t graph_id,
                     int mode, uint64_t* ticket);
 /* Non-blocking: *done = 1 when the request finished, with its count and status. */
-int tc_serve_poll(tc_server* s, uint64_t ticket, int* done, uint64_t* count, int* status);
-int tc_serve_destroy(tc_server* s);
+TC_API int tc_serve_poll(tc_server* s, uint64_t ticket, int* done, uint64_t* count, int* status);
+TC_API int tc_serve_destroy(tc_server* s);
 
 #ifdef __cplusplus
 }

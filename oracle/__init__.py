@@ -9,11 +9,11 @@ code with it.
 
 Functions (each cites the passage it follows in ``oracle.c``):
 
-* :func:`bfs_levels` — Def. 2 / Alg. 1 lines 2-3, with the root rule
+* :func:`bfs_levels` — Def. 2 / Alg. 1, with the root rule
   "maximum-degree vertex first (lowest id on ties), then every other
   component rooted at its lowest id".
-* :func:`cover_edges` — Thm. 1 / Alg. 1 lines 4-5.
-* :func:`cetc_count`, :func:`cetc_edge_counts` — Alg. 1 lines 6-8.
+* :func:`cover_edges` — Thm. 1 / Alg. 1.
+* :func:`cetc_count`, :func:`cetc_edge_counts` — Alg. 1.
 * :func:`plain_count` — the direction-oriented edge iterator (Sec. I, V-A).
 * :func:`triangles` — triangle finding (lists {a < b < c}).
 """
@@ -74,7 +74,7 @@ class Oracle:
         self.lib = lib
 
     def bfs_levels(self, g, roots=None):
-        """Levels L[n] (uint32) and the number of levels (Def. 2, Alg. 1 l.2-3)."""
+        """Levels L[n] (uint32) and the number of levels (Def. 2, Alg. 1)."""
         off, cols = _csr(g)
         L = np.empty(max(g.n, 1), dtype=np.uint32)
         if roots is None:
@@ -101,7 +101,7 @@ class Oracle:
         return uv[:h]
 
     def cetc_count(self, g, L) -> int:
-        """T by Alg. 1 lines 4-8 (exact uint64)."""
+        """T by Alg. 1 (exact uint64)."""
         off, cols = _csr(g)
         L = np.ascontiguousarray(L, dtype=np.uint32)
         if L.size == 0:
@@ -109,7 +109,7 @@ class Oracle:
         return int(self.lib.or_cetc_count(g.n, _i64(off), _u32(cols), _u32(L)))
 
     def cetc_edge_counts(self, g, L, uv) -> np.ndarray:
-        """Per-cover-edge counts (Alg. 1 line 7) for the given (k, 2) edge list."""
+        """Per-cover-edge counts (Alg. 1) for the given (k, 2) edge list."""
         off, cols = _csr(g)
         L = np.ascontiguousarray(L, dtype=np.uint32)
         uv = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)

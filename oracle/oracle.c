@@ -10,13 +10,13 @@
  * Source: D. A. Bader et al., "Triangle Counting Through Cover-Edges"
  * (arXiv 2210.00389).  Every function below cites the passage it follows.
  *
- * Input everywhere: a simple undirected graph as a symmetric CSR
- * (Sec. III-B: "The input graph G is stored in a compressed sparse row (CSR)
- * format"): off[n+1] (int64), cols[off[n]] (uint32), each row sorted
- * ascending with no duplicates and no self-loops.
+ * Input everywhere: a simple undirected graph held in compressed sparse row
+ * form, the input format of Sec. III, made symmetric: off[n+1] (int64),
+ * cols[off[n]] (uint32), each row sorted ascending with no duplicates and
+ * no self-loops.
  *
  * Readings of the paper taken here (the paper is silent on them):
- *   - Root rule.  Alg. 1 starts a BFS "from any unvisited vertex".  The first
+ *   - Root rule.  Alg. 1 launches a BFS from an arbitrary vertex not yet reached.  The first
  *     root is the vertex of maximum degree (lowest id on ties); after its
  *     component, vertices are scanned in ascending id order and every still
  *     unvisited one starts a new BFS, i.e. every other component is rooted
@@ -38,7 +38,7 @@
 #define OR_UNVISITED 0xFFFFFFFFu
 
 /* ------------------------------------------------------------------------ */
-/* Def. 2 + Alg. 1 (lines 2-3): BFS levels, restarted from every unvisited
+/* Def. 2 + Alg. 1: BFS levels, restarted from every unvisited
  * vertex.  L[v] = shortest distance from the root of v's component.
  * Returns the number of levels (1 + max L), 0 for n = 0, -1 on bad input. */
 static void bfs_from(uint32_t root, const int64_t* off, const uint32_t* cols,
@@ -77,7 +77,7 @@ OR_EXPORT int64_t or_bfs_levels(uint32_t n, const int64_t* off, const uint32_t* 
       if (off[v + 1] - off[v] > off[r0 + 1] - off[r0]) r0 = v;
     bfs_from(r0, off, cols, L, queue);
   }
-  /* Alg. 1 line 2-3: every vertex still unvisited starts its own BFS */
+  /* Alg. 1: every vertex still unvisited starts its own BFS */
   for (uint32_t v = 0; v < n; ++v)
     if (L[v] == OR_UNVISITED) bfs_from(v, off, cols, L, queue);
 
@@ -88,10 +88,10 @@ OR_EXPORT int64_t or_bfs_levels(uint32_t n, const int64_t* off, const uint32_t* 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Thm. 1 + Alg. 1 (lines 4-5): the cover-edge set H = horizontal edges,
+/* Thm. 1 + Alg. 1: the cover-edge set H = horizontal edges,
  * {(u,v) in E : L(u) = L(v), u < v}, emitted in ascending (u, v) order.
- * A tree edge always joins adjacent levels, so "non-tree edge with both ends
- * on one level" (Def. 2) is exactly "both ends on one level".
+ * A tree edge always joins adjacent levels, so the horizontal edges of
+ * Def. 2 (non-tree edges inside one level) are all edges inside one level.
  * Writes at most cap pairs (uv[2i] = u, uv[2i+1] = v); returns |H|. */
 OR_EXPORT int64_t or_cover_edges(uint32_t n, const int64_t* off, const uint32_t* cols,
                                  const uint32_t* L, uint32_t* uv, int64_t cap) {
@@ -109,7 +109,7 @@ OR_EXPORT int64_t or_cover_edges(uint32_t n, const int64_t* off, const uint32_t*
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 1 (lines 6-8) for one cover edge (u, v), u < v, L(u) = L(v):
+/* Alg. 1 for one cover edge (u, v), u < v, L(u) = L(v):
  * the number of w in N(u) ∩ N(v) with L(u) != L(w), or L(u) = L(w) and
  * v < w.  N(u) ∩ N(v) is found by the two-pointer merge of the two sorted
  * adjacency lists (merge-path intersection, Sec. V-A). */
@@ -146,7 +146,7 @@ OR_EXPORT uint64_t or_cetc_count(uint32_t n, const int64_t* off, const uint32_t*
   return T;
 }
 
-/* Per-edge counts of Alg. 1 line 7 for an explicit list of k cover edges
+/* Per-edge counts of Alg. 1 for an explicit list of k cover edges
  * (uv[2i], uv[2i+1]).  Returns -1 if an entry is not a cover edge (u >= v,
  * levels differ or (u, v) not in E), else 0. */
 OR_EXPORT int or_cetc_edge_counts(uint32_t n, const int64_t* off, const uint32_t* cols,
@@ -155,9 +155,13 @@ OR_EXPORT int or_cetc_edge_counts(uint32_t n, const int64_t* off, const uint32_t
   for (int64_t i = 0; i < k; ++i) {
     uint32_t u = uv[2 * i], v = uv[2 * i + 1];
     if (u >= n || v >= n || !(u < v) || L[u] != L[v]) return -1;
-    int found = 0;
-    for (int64_t e = off[u]; e < off[u + 1]; ++e) if (cols[e] == v) { found = 1; break; }
-    if (!found) return -1;
+    /* membership of v in N(u) by bisection of the sorted row */
+    int64_t lo = off[u], hi = off[u + 1];
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (cols[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    if (!(lo < off[u + 1] && cols[lo] == v)) return -1;
     counts[i] = (uint32_t)cover_edge_count(off, cols, L, u, v);
   }
   return 0;

@@ -1,0 +1,130 @@
+// C ABI entry points for levels, cover edges and counts (include/tc.h).
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace tc {
+
+// Makes the graph's device current for the scope of a call.
+struct DeviceGuard {
+  int prev = -1, want;
+  explicit DeviceGuard(int dev) : want(dev) {
+    cudaGetDevice(&prev);
+    if (prev != want) cudaSetDevice(want);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0 && prev != want) cudaSetDevice(prev);
+  }
+};
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    ms = 0.f;
+  }
+  return ms;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+int tc_bfs_levels(tc_graph* g, const uint32_t* roots, uint32_t nroots, uint32_t* levels_out,
+                  uint32_t* nlevels_out) {
+  if (!g) return fail(TC_ERR_INVALID_ARG, "tc_bfs_levels: NULL graph");
+  if (roots && nroots == 0) roots = nullptr;
+  DeviceGuard dg(g->device);
+  cudaEventRecord(g->ev[0], g->stream);
+  TC_TRY(compute_levels(g, roots, nroots));
+  cudaEventRecord(g->ev[1], g->stream);
+  if (levels_out && g->n > 0) {
+    TC_CUDA(copy_out(levels_out, g->levels.p, sizeof(uint32_t) * g->n, g->stream));
+  }
+  TC_CUDA(cudaStreamSynchronize(g->stream));
+  g->stats.ms_bfs = elapsed(g->ev[0], g->ev[1]);
+  if (nlevels_out) *nlevels_out = (uint32_t)g->nlevels;
+  return TC_OK;
+}
+
+int tc_cover_edges(tc_graph* g, uint32_t* uv_out, int64_t cap, int64_t* count_out) {
+  if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_cover_edges: NULL argument");
+  if (uv_out && cap < 0) return fail(TC_ERR_INVALID_ARG, "tc_cover_edges: cap < 0");
+  DeviceGuard dg(g->device);
+  cudaEventRecord(g->ev[0], g->stream);
+  if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
+  cudaEventRecord(g->ev[1], g->stream);
+  if (g->num_cover < 0) TC_TRY(compute_cover(g));
+  cudaEventRecord(g->ev[2], g->stream);
+  *count_out = g->num_cover;
+  if (uv_out) {
+    if (g->num_cover > cap) {
+      TC_CUDA(cudaStreamSynchronize(g->stream));
+      return fail(TC_ERR_CAPACITY, "tc_cover_edges: |H| = %lld > cap = %lld",
+                  (long long)g->num_cover, (long long)cap);
+    }
+    TC_CUDA(copy_out(uv_out, g->cover.p, sizeof(uint2) * (size_t)g->num_cover, g->stream));
+  }
+  TC_CUDA(cudaStreamSynchronize(g->stream));
+  g->stats.ms_bfs = elapsed(g->ev[0], g->ev[1]);
+  g->stats.ms_cover = elapsed(g->ev[1], g->ev[2]);
+  return TC_OK;
+}
+
+int tc_count(tc_graph* g, int mode, uint64_t* count_out) {
+  if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_count: NULL argument");
+  if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
+    return fail(TC_ERR_INVALID_ARG, "tc_count: unknown mode %d", mode);
+  DeviceGuard dg(g->device);
+  tc_stats_t& st = g->stats;
+  st.ms_bfs = st.ms_cover = st.ms_bucket = st.ms_intersect = st.ms_total = 0.f;
+  const unsigned long long launches0 = g_kernel_launches.load();
+  uint64_t T = 0;
+  cudaEventRecord(g->ev[0], g->stream);
+  if (mode == TC_MODE_COVER) {
+    if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
+    cudaEventRecord(g->ev[1], g->stream);
+    if (g->num_cover < 0) TC_TRY(compute_cover(g));
+    cudaEventRecord(g->ev[2], g->stream);
+    TC_TRY(count_cover(g, nullptr, &T));
+    cudaEventRecord(g->ev[3], g->stream);
+    cudaEventSynchronize(g->ev[3]);
+    st.ms_bfs = elapsed(g->ev[0], g->ev[1]);
+    st.ms_cover = elapsed(g->ev[1], g->ev[2]);
+    st.ms_total = elapsed(g->ev[0], g->ev[3]);
+  } else {
+    cudaEventRecord(g->ev[1], g->stream);
+    TC_TRY(count_plain(g, &T));
+    cudaEventRecord(g->ev[3], g->stream);
+    cudaEventSynchronize(g->ev[3]);
+    st.ms_total = elapsed(g->ev[0], g->ev[3]);
+  }
+  st.kernel_launches = (uint32_t)(g_kernel_launches.load() - launches0);
+  *count_out = T;
+  return TC_OK;
+}
+
+int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap) {
+  if (!g || !counts_out) return fail(TC_ERR_INVALID_ARG, "tc_cover_edge_counts: NULL argument");
+  DeviceGuard dg(g->device);
+  if (g->num_cover < 0) TC_TRY(compute_cover(g));
+  if (g->num_cover > cap)
+    return fail(TC_ERR_CAPACITY, "tc_cover_edge_counts: |H| = %lld > cap = %lld",
+                (long long)g->num_cover, (long long)cap);
+  if (g->num_cover == 0) return TC_OK;
+  uint64_t T = 0;
+  if (is_device_ptr(counts_out)) {
+    TC_TRY(count_cover(g, counts_out, &T));
+  } else {
+    DevBuf<uint32_t> tmp;
+    TC_TRY(tmp.alloc((size_t)g->num_cover, g->stream));
+    TC_TRY(count_cover(g, tmp.p, &T));
+    TC_CUDA(copy_out(counts_out, tmp.p, sizeof(uint32_t) * (size_t)g->num_cover, g->stream));
+    TC_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  return TC_OK;
+}
+
+}  // extern "C"

@@ -13,8 +13,9 @@ Also measured in the same run:
   * end to end through the C ABI with pinned HOST buffers (H2D copy of the
     CSR and D2H of the count inside the timed region);
   * the intersection kernel's duration (CUDA events on its stream) against
-    the HBM roofline, with algorithmic bytes per launch
-    sum over cover edges of (4 d(u) + 4 d(v) + 16) + 4 * matches + 8 |H|;
+    the HBM roofline, with algorithmic bytes per launch = 4 B per list
+    element the kernel must stream (level segments of both endpoints,
+    counted by the kernel) + 72 B of per-edge metadata;
   * the CPU oracle on a bounded sample of the same workload (rank 0, N=1).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -48,8 +49,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "rmat10", "chunglu23",
-                                                              "rmat18"])
+    ap.add_argument("--workload", default="rmat22",
+                    choices=["rmat22", "rmat10", "rmat18", "rmat20", "chunglu23"])
+    ap.add_argument("--arm", default="all", choices=["all", "cover", "plain"],
+                    help="'cover' or 'plain' runs only that device-resident arm "
+                         "(for profiling one step); 'all' is the benchmark")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -65,9 +69,10 @@ def make_graph(workload: str, rank: int):
         g = gg.rmat(22, 16, seed, relabel_seed=seed + 2**32)
         desc = ("R-MAT scale 22, edgefactor 16, a/b/c/d=.57/.19/.19/.05, edge seed %d, "
                 "relabel stream %d+2^32, symmetrised, deduplicated" % (seed, seed))
-    elif workload == "rmat18":
-        g = gg.rmat(18, 16, 2 + rank * 1000, relabel_seed=2 + rank * 1000 + 2**32)
-        desc = "R-MAT scale 18, edgefactor 16, relabelled"
+    elif workload in ("rmat18", "rmat20"):
+        sc = int(workload[4:])
+        g = gg.rmat(sc, 16, 2 + rank * 1000, relabel_seed=2 + rank * 1000 + 2**32)
+        desc = f"R-MAT scale {sc}, edgefactor 16, relabelled"
     elif workload == "rmat10":
         g = gg.rmat(10, 16, 1 + rank * 1000)
         desc = "R-MAT scale 10, edgefactor 16, seed 1"
@@ -322,6 +327,15 @@ def run_ours(args, world, rank, local):
         ms = e0.elapsed_time(e1) / args.steps
         return ms, res, tc.tc_kernel_launches() - l0
 
+    if args.arm != "all":
+        mode = tc.TC_MODE_COVER if args.arm == "cover" else tc.TC_MODE_PLAIN
+        ms, res, launches = timed(mode)
+        if rank == 0:
+            print(json.dumps({"arm": args.arm, "ms_per_step": ms, "triangles": res[0][0],
+                              "stats": res[0][1], "gpu_launches": launches,
+                              "workload": desc}), flush=True)
+        return
+
     sampler = ClockSampler(gpu_uuid(torch, dev))
     sampler.start()
     ms_cover, res_cover, launches = timed(tc.TC_MODE_COVER)
@@ -339,21 +353,32 @@ def run_ours(args, world, rank, local):
     units = reduce_sum(float(g.num_edges), world, dev)
     value = units / (ms_cover_max / 1e3)
 
-    # roofline of the dominant kernel (the cover intersection)
+    # roofline of the dominant kernel (the cover intersection).  Algorithmic
+    # bytes per launch: the list elements it must stream (4 B each, counted
+    # by the kernel) plus 72 B of per-edge metadata (H entry, two offset
+    # pairs, two segment descriptors).
     st0, info0 = res_cover[0][1], res_cover[0][2]
     ms_k = statistics.mean(r[1]["ms_intersect"] for r in res_cover)
+    nh = info0["num_cover"]
+    alg_bytes = float(4 * st0["list_elems"] + 72 * nh)
     with tc.Graph(off_d, cols_d, g.n, tc.TC_GRAPH_BORROW, stream) as G:
         H = G.cover_edges()
     deg = g.degrees()
     u = H[:, 0].astype(np.int64)
     v = H[:, 1].astype(np.int64)
-    alg_bytes = float((4 * deg[u] + 4 * deg[v] + 16).sum() + 4 * st0["matches"] + 8 * len(H))
+    merge_bytes = float((4 * deg[u] + 4 * deg[v] + 16).sum() + 8 * len(H))
+    del H, u, v
     peak, peak_kind = measured_hbm_peak()
     achieved = alg_bytes / (ms_k / 1e3) / 1e9
-    tr = ncu_traffic("k_cover_bsearch")
+    stp = res_plain[0][1]
+    ms_kp = statistics.mean(r[1]["ms_intersect"] for r in res_plain)
+    plain_bytes = float(4 * stp["list_elems"] + 32 * g.nnz)
+    tr = ncu_traffic("k_cover_intersect")
     stages = {k: statistics.mean(r[1][k] for r in res_cover)
               for k in ("ms_bfs", "ms_cover", "ms_intersect", "ms_total")}
-    stages_plain = {"ms_intersect": statistics.mean(r[1]["ms_intersect"] for r in res_plain)}
+    stages_plain = {"ms_intersect": ms_kp,
+                    "intersect_GBps": plain_bytes / (ms_kp / 1e3) / 1e9,
+                    "list_elems": stp["list_elems"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -380,10 +405,12 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": units / (ms_e2e_max / 1e3), "unit": "edges/s",
                 "ms_per_step": ms_e2e_max, "h2d_bytes_per_step": csr_bytes,
                 "d2h_bytes_per_step": 8},
-        "roofline": {"bound": "hbm", "kernel": "k_cover_bsearch", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "k_cover_intersect", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "frac_of_8tbs_nominal": achieved / 8000.0,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": ms_k,
+                     "list_elems": st0["list_elems"],
+                     "merge_equivalent_bytes": merge_bytes,
                      "traffic": tr["bytes_per_launch"] if tr else None,
                      "traffic_source": tr.get("source") if tr else None},
         "gpu_launches": launches,

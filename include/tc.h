@@ -172,7 +172,7 @@ typedef struct {
   uint32_t bfs_bottom_up;     /* of which bottom-up */
   int64_t edges_intersected;  /* |H| (cover) or |E| (plain) */
   int64_t list_elems;         /* sum of list lengths handed to the intersection */
-  uint64_t matches;           /* common neighbours found before the predicate */
+  uint64_t reserved0;
   uint32_t kernel_launches;   /* kernels launched by the call */
 } tc_stats_t;
 TC_API int tc_graph_stats(const tc_graph* g, tc_stats_t* out);

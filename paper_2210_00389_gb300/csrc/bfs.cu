@@ -225,6 +225,7 @@ int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots) {
   const uint32_t n = g->n;
   g->cover.release();
   g->num_cover = -1;
+  g->seg_valid = false;
   g->nlevels = -1;
   g->stats.bfs_levels = 0;
   g->stats.bfs_bottom_up = 0;

@@ -203,7 +203,11 @@ void graph_drop_cache(tc_graph* g) {
   g->nlevels = -1;
   g->nroots = 0;
   g->cover.release();
+  g->hoff.release();
   g->num_cover = -1;
+  g->seg_valid = false;
+  g->scols.release();
+  g->seg.release();
 }
 
 }  // namespace tc

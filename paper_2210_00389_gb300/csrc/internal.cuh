@@ -116,8 +116,14 @@ struct tc_graph {
   int64_t nlevels = -1;
   uint32_t nroots = 0;
 
+  // cached level-segmented adjacency (see segment.cu)
+  tc::DevBuf<uint32_t> scols;
+  tc::DevBuf<uint4> seg;
+  bool seg_valid = false;
+
   // cached cover-edge set H as (u, v) pairs in CSR order
   tc::DevBuf<uint2> cover;
+  tc::DevBuf<unsigned long long> hoff;  // index in H of each vertex's first cover edge
   int64_t num_cover = -1;
 
   // small control block on device + pinned host mirror
@@ -140,8 +146,9 @@ enum CtrlSlot {
   kCtrlQ0 = 3,        // BFS: next-frontier size
   kCtrlQ1 = 4,        // BFS: next-frontier edge sum
   kCtrlMax = 5,       // argmax key
-  kCtrlMatches = 6,   // common neighbours before the predicate
+  kCtrlElems = 6,     // list elements handed to the intersection
   kCtrlTmp = 7,
+  kCtrlWork = 8,      // dynamic work counter of the intersection kernels
   kCtrlSlots = 16
 };
 
@@ -157,6 +164,7 @@ enum : unsigned long long {
 
 // stage functions (each returns TC_OK or an error)
 int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots);
+int compute_segments(tc_graph* g);
 int compute_cover(tc_graph* g);
 int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total);
 int count_plain(tc_graph* g, uint64_t* total);

@@ -1,30 +1,33 @@
-// Intersection + count-once rule (a4) and reduction (a5); plain count (a6).
+// Intersection + count-once rule (a4), reduction (a5), plain count (a6).
 //
-// Cover path, Alg. 1 and Thm. 2 of Bader et al., "Triangle
-// Counting Through Cover-Edges": for each cover edge (u, v), u < v,
-// c_uv = |{ w in N(u) ∩ N(v) : L(w) != L(u)  or  w > v }|, T = sum c_uv.
-// Plain path, the direction-oriented edge iterator (Sec. I, Sec. V-A): for
-// each edge u < v, |{ w in N(u) ∩ N(v) : w > v }|.
+// Cover path (Alg. 1 and Thm. 2 of Bader et al., "Triangle Counting Through
+// Cover-Edges"): for a cover edge (u, v), u < v, on level l,
+//   c_uv = |{ w in N(u) ∩ N(v) : L(w) != l  or  w > v }|.
+// A common neighbour lies on level l-1, l or l+1, so with the level-segmented
+// rows of segment.cu
+//   c_uv = |N_{l-1}(u) ∩ N_{l-1}(v)| + |N_{l+1}(u) ∩ N_{l+1}(v)|
+//        + |N_l(u) ∩ (v,inf)  ∩  N_l(v) ∩ (v,inf)|.
+// Plain path (direction-oriented edge iterator, Sec. I and Sec. V-A): for an
+// edge u < v, |N(u) ∩ (v,inf) ∩ N(v) ∩ (v,inf)|.
 //
-// Intersection by binary search of the shorter list in the longer one
-// (Sec. V-A, "binary-search algorithms"), one warp per edge: every lane
-// takes elements of the short list.  Warp-shuffle reduction to one 64-bit
-// atomic per block; counts are exact integers, so the order is irrelevant.
+// Both paths share one warp-cooperative intersection of two sorted lists
+// (warp_intersect): a windowed merge that streams both lists 32 elements at
+// a time (merge-path, Sec. V-A) when their lengths are within a factor
+// kSkew, else a binary search of the shorter list in the longer one
+// (binary-search intersection, Sec. V-A).  Edges are handed to warps in
+// chunks from an atomic work counter (dynamic load balance; consecutive
+// edges share an endpoint, so its rows stay in L1).  Per-lane counts are
+// reduced by warp shuffles, then one 64-bit atomic per block; counts are
+// exact integers, so the summation order does not matter.
 #include "internal.cuh"
 
 namespace tc {
 
 constexpr int kIsThreads = 256;
-
-__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* __restrict__ a, int64_t len,
-                                                   uint32_t x) {
-  int64_t lo = 0, hi = len;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
+constexpr uint32_t kInf = 0xFFFFFFFFu;  // never a vertex id (n < 2^32 - 1)
+constexpr int64_t kSkew = 24;           // merge when max(len) <= kSkew * min(len)
+constexpr int kCoverChunk = 8;          // cover edges per work grab
+constexpr int kPlainChunk = 64;         // CSR entries per work grab
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
@@ -44,43 +47,106 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
   }
 }
 
-// One warp per cover edge.
-__global__ void __launch_bounds__(kIsThreads)
-k_cover_bsearch(const uint2* __restrict__ H, int64_t nh, const int64_t* __restrict__ off,
-                const uint32_t* __restrict__ cols, const uint32_t* __restrict__ L,
-                uint32_t* __restrict__ per_edge, unsigned long long* ctrl) {
+// |A ∩ B| for strictly ascending A[0..la), B[0..lb).  All 32 lanes call it
+// with identical arguments; each returns its share of the count.
+__device__ __forceinline__ unsigned warp_intersect(const uint32_t* __restrict__ A, int64_t la,
+                                                   const uint32_t* __restrict__ B, int64_t lb) {
   const int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long acc = 0, matches = 0;
-  for (int64_t i = warp; i < nh; i += nwarps) {
-    const uint2 e = H[i];
-    const uint32_t u = e.x, v = e.y;
-    const int64_t bu = off[u], du = off[u + 1] - bu;
-    const int64_t bv = off[v], dv = off[v + 1] - bv;
-    const uint32_t* A = cols + (du <= dv ? bu : bv);
-    const uint32_t* B = cols + (du <= dv ? bv : bu);
-    const int64_t la = du <= dv ? du : dv, lb = du <= dv ? dv : du;
-    const uint32_t lvl = L[u];
-    unsigned c = 0, m = 0;
+  if (la > lb) {
+    const uint32_t* t = A; A = B; B = t;
+    int64_t tl = la; la = lb; lb = tl;
+  }
+  if (la == 0) return 0;
+  unsigned cnt = 0;
+  if (lb > kSkew * la) {
+    // skewed: every lane binary-searches its elements of A in B; a lane's
+    // elements increase, so its search window starts where the last ended
+    int64_t lo = 0;
     for (int64_t k = lane; k < la; k += 32) {
-      const uint32_t x = A[k];
-      const int64_t p = lower_bound_u32(B, lb, x);
-      if (p < lb && B[p] == x) {
-        ++m;
-        if (L[x] != lvl || x > v) ++c;
+      const uint32_t x = __ldg(A + k);
+      int64_t hi = lb;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(B + mid) < x) lo = mid + 1; else hi = mid;
       }
+      if (lo < lb && __ldg(B + lo) == x) ++cnt;
     }
-    unsigned long long cs = warp_sum(c);
-    matches += m;
-    if (lane == 0) {
-      if (per_edge) per_edge[i] = (uint32_t)cs;
-      acc += cs;
+    return cnt;
+  }
+  // windowed merge: a holds A[ia + lane], b holds B[ib + lane]
+  int64_t ia = 0, ib = 0;
+  uint32_t a = lane < la ? __ldg(A + lane) : kInf;
+  uint32_t b = lane < lb ? __ldg(B + lane) : kInf;
+  while (true) {
+    const int a_last = (int)min((int64_t)31, la - 1 - ia);
+    const int b_last = (int)min((int64_t)31, lb - 1 - ib);
+    const uint32_t amax = __shfl_sync(0xFFFFFFFFu, a, a_last);
+    const uint32_t bmax = __shfl_sync(0xFFFFFFFFu, b, b_last);
+    // rank of a among the 32 window values (sorted, kInf padded)
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      const uint32_t bv = __shfl_sync(0xFFFFFFFFu, b, pos + s - 1);
+      if (bv < a) pos += s;
+    }
+    const uint32_t bv = __shfl_sync(0xFFFFFFFFu, b, pos);
+    if (lane <= a_last && bv == a) ++cnt;
+    const bool adv_a = amax <= bmax, adv_b = bmax <= amax;
+    if (adv_a) {
+      ia += 32;
+      if (ia >= la) break;
+      a = ia + lane < la ? __ldg(A + ia + lane) : kInf;
+    }
+    if (adv_b) {
+      ib += 32;
+      if (ib >= lb) break;
+      b = ib + lane < lb ? __ldg(B + ib + lane) : kInf;
+    }
+  }
+  return cnt;
+}
+
+// Cover edges, warp per edge, chunks grabbed from *work.
+__global__ void __launch_bounds__(kIsThreads)
+k_cover_intersect(const uint2* __restrict__ H, int64_t nh, const int64_t* __restrict__ off,
+                  const uint32_t* __restrict__ scols, const uint4* __restrict__ seg,
+                  const unsigned long long* __restrict__ hoff,
+                  uint32_t* __restrict__ per_edge, unsigned long long* work,
+                  unsigned long long* ctrl) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long acc = 0, elems = 0;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(work, (unsigned long long)kCoverChunk);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if ((int64_t)base >= nh) break;
+    const int64_t end = min((int64_t)base + kCoverChunk, nh);
+    for (int64_t i = (int64_t)base; i < end; ++i) {
+      const uint2 e = H[i];
+      const int64_t ou = off[e.x], eu = off[e.x + 1];
+      const int64_t ov = off[e.y], ev = off[e.y + 1];
+      const uint4 su = seg[e.x], sv = seg[e.y];
+      const uint32_t* Ru = scols + ou;
+      const uint32_t* Rv = scols + ov;
+      // v is entry (i - hoff[u]) of u's same-level run above u, so the
+      // same-level ids of u greater than v start right after it
+      const uint32_t cut = su.y + (uint32_t)(i - (int64_t)hoff[e.x]) + 1u;
+      unsigned c = warp_intersect(Ru, su.x, Rv, sv.x);                      // level l-1
+      c += warp_intersect(Ru + cut, su.z - cut, Rv + sv.y, sv.z - sv.y);    // level l, > v
+      c += warp_intersect(Ru + su.z, (eu - ou) - su.z, Rv + sv.z, (ev - ov) - sv.z);  // l+1
+      acc += c;
+      if (lane == 0)
+        elems += (unsigned long long)(su.x + sv.x + (su.z - cut) + (sv.z - sv.y)) +
+                 (unsigned long long)((eu - ou) - su.z + (ev - ov) - sv.z);
+      if (per_edge) {
+        const unsigned long long t = warp_sum(c);
+        if (lane == 0) per_edge[i] = (uint32_t)t;
+      }
     }
   }
   block_add(acc, &ctrl[kCtrlCount]);
   __syncthreads();
-  block_add(matches, &ctrl[kCtrlMatches]);
+  block_add(elems, &ctrl[kCtrlElems]);
 }
 
 // ustart[v] = index (into cols) of the first neighbour of v greater than v.
@@ -89,49 +155,53 @@ __global__ void k_upper_start(const int64_t* __restrict__ off, const uint32_t* _
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; v < (int64_t)n; v += stride) {
-    const int64_t b = off[v];
-    ustart[v] = b + lower_bound_u32(cols + b, off[v + 1] - b, (uint32_t)v + 1u);
+    int64_t lo = off[v], hi = off[v + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (cols[mid] <= (uint32_t)v) lo = mid + 1; else hi = mid;
+    }
+    ustart[v] = lo;
   }
 }
 
-// One warp per CSR entry (u, v) with u < v: |N(u) ∩ N(v) ∩ (v, inf)|, where
-// both suffixes start after v (N(u) right after the entry itself).
+// Plain edge iterator: warp per CSR entry (u, v) with u < v.
 __global__ void __launch_bounds__(kIsThreads)
-k_plain_bsearch(const uint32_t* __restrict__ erow, int64_t nnz, const int64_t* __restrict__ off,
-                const uint32_t* __restrict__ cols, const int64_t* __restrict__ ustart,
-                unsigned long long* ctrl) {
+k_plain_intersect(const uint32_t* __restrict__ erow, int64_t nnz, const int64_t* __restrict__ off,
+                  const uint32_t* __restrict__ cols, const int64_t* __restrict__ ustart,
+                  unsigned long long* work, unsigned long long* ctrl) {
   const int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long acc = 0;
-  for (int64_t e = warp; e < nnz; e += nwarps) {
-    const uint32_t u = erow[e], v = cols[e];
-    if (u >= v) continue;
-    const int64_t au = e + 1, du = off[u + 1] - au;
-    const int64_t av = ustart[v], dv = off[v + 1] - av;
-    const uint32_t* A = cols + (du <= dv ? au : av);
-    const uint32_t* B = cols + (du <= dv ? av : au);
-    const int64_t la = du <= dv ? du : dv, lb = du <= dv ? dv : du;
-    unsigned c = 0;
-    for (int64_t k = lane; k < la; k += 32) {
-      const uint32_t x = A[k];
-      const int64_t p = lower_bound_u32(B, lb, x);
-      if (p < lb && B[p] == x) ++c;
+  unsigned long long acc = 0, elems = 0;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(work, (unsigned long long)kPlainChunk);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if ((int64_t)base >= nnz) break;
+    const int64_t end = min((int64_t)base + kPlainChunk, nnz);
+    for (int64_t e = (int64_t)base; e < end; ++e) {
+      const uint32_t u = erow[e], v = cols[e];
+      if (u >= v) continue;
+      const int64_t au = e + 1, bv = ustart[v];
+      const int64_t la = off[u + 1] - au, lb = off[v + 1] - bv;
+      acc += warp_intersect(cols + au, la, cols + bv, lb);
+      if (lane == 0) elems += (unsigned long long)(la + lb);
     }
-    acc += c;
   }
   block_add(acc, &ctrl[kCtrlCount]);
+  __syncthreads();
+  block_add(elems, &ctrl[kCtrlElems]);
 }
 
 int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
   cudaStream_t s = g->stream;
   if (g->num_cover < 0) TC_TRY(compute_cover(g));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
-  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlMatches, 0, sizeof(unsigned long long), s));
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
   cudaEventRecord(g->ev[4], s);
   if (g->num_cover > 0) {
-    launch(k_cover_bsearch, grid_for(g->num_cover * 32, kIsThreads, 8), kIsThreads, 0, s, 
-        g->cover.p, g->num_cover, g->off, g->cols, g->levels.p, per_edge_out, g->ctrl.p);
+    launch(k_cover_intersect, grid_for(g->num_cover * 32, kIsThreads, 8), kIsThreads, 0, s,
+           g->cover.p, g->num_cover, g->off, g->scols.p, g->seg.p, g->hoff.p, per_edge_out,
+           g->ctrl.p + kCtrlWork, g->ctrl.p);
     TC_CUDA(cudaGetLastError());
   }
   cudaEventRecord(g->ev[5], s);
@@ -139,8 +209,8 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
                           cudaMemcpyDeviceToHost, s));
   TC_CUDA(cudaStreamSynchronize(s));
   *total = g->ctrl_host[kCtrlCount];
-  g->stats.matches = g->ctrl_host[kCtrlMatches];
   g->stats.edges_intersected = g->num_cover;
+  g->stats.list_elems = (int64_t)g->ctrl_host[kCtrlElems];
   cudaEventElapsedTime(&g->stats.ms_intersect, g->ev[4], g->ev[5]);
   return TC_OK;
 }
@@ -148,14 +218,17 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
 int count_plain(tc_graph* g, uint64_t* total) {
   cudaStream_t s = g->stream;
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
+  g->stats.ms_intersect = 0.f;
   if (g->nnz > 0) {
     DevBuf<int64_t> ustart;
     TC_TRY(ustart.alloc(g->n, s));
     launch(k_upper_start, grid_for(g->n, kIsThreads), kIsThreads, 0, s, g->off, g->cols, g->n,
-                                                                     ustart.p);
+           ustart.p);
     cudaEventRecord(g->ev[4], s);
-    launch(k_plain_bsearch, grid_for(g->nnz * 32, kIsThreads, 8), kIsThreads, 0, s, 
-        g->erow.p, g->nnz, g->off, g->cols, ustart.p, g->ctrl.p);
+    launch(k_plain_intersect, grid_for(g->nnz * 32, kIsThreads, 8), kIsThreads, 0, s, g->erow.p,
+           g->nnz, g->off, g->cols, ustart.p, g->ctrl.p + kCtrlWork, g->ctrl.p);
     TC_CUDA(cudaGetLastError());
     cudaEventRecord(g->ev[5], s);
   }
@@ -164,6 +237,7 @@ int count_plain(tc_graph* g, uint64_t* total) {
   TC_CUDA(cudaStreamSynchronize(s));
   *total = g->ctrl_host[kCtrlCount];
   g->stats.edges_intersected = g->nnz / 2;
+  g->stats.list_elems = (int64_t)g->ctrl_host[kCtrlElems];
   if (g->nnz > 0) cudaEventElapsedTime(&g->stats.ms_intersect, g->ev[4], g->ev[5]);
   return TC_OK;
 }

@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "cover-edge TC edges/s, % HBM roofline vs plain all-edge GPU TC; serve p50/p99"
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
-INTERSECT_SOURCE = os.path.join(ROOT, "paper_2210_00389_gb300", "csrc", "intersect.cu")
+INTERSECT_SOURCE = os.path.join(ROOT, "paper_2210_00389_gb300", "csrc", "hashsect.cu")
 
 
 def parse_args():
@@ -353,12 +353,12 @@ def run_ours(args, world, rank, local):
     units = reduce_sum(float(g.num_edges), world, dev)
     value = units / (ms_cover_max / 1e3)
 
-    # roofline of the dominant kernel (the cover intersection).  Algorithmic
-    # bytes per launch: the list elements it must stream (4 B each, counted
-    # by the kernel) plus 72 B of per-edge metadata (H entry, two offset
-    # pairs, two segment descriptors).
+    # roofline of the dominant kernel (the cover hash intersection).
+    # Algorithmic bytes per launch: 4 B per probe-list element it must read
+    # (counted by the kernel) plus 72 B of per-edge metadata (task index,
+    # H entry, two offset pairs, segment descriptor, H offset).
     st0, info0 = res_cover[0][1], res_cover[0][2]
-    ms_k = statistics.mean(r[1]["ms_intersect"] for r in res_cover)
+    ms_k = statistics.mean(r[1]["ms_main_kernel"] for r in res_cover)
     nh = info0["num_cover"]
     alg_bytes = float(4 * st0["list_elems"] + 72 * nh)
     with tc.Graph(off_d, cols_d, g.n, tc.TC_GRAPH_BORROW, stream) as G:
@@ -371,11 +371,11 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_hbm_peak()
     achieved = alg_bytes / (ms_k / 1e3) / 1e9
     stp = res_plain[0][1]
-    ms_kp = statistics.mean(r[1]["ms_intersect"] for r in res_plain)
-    plain_bytes = float(4 * stp["list_elems"] + 32 * g.nnz)
-    tr = ncu_traffic("k_cover_intersect")
+    ms_kp = statistics.mean(r[1]["ms_main_kernel"] for r in res_plain)
+    plain_bytes = float(4 * stp["list_elems"] + 72 * g.num_edges)
+    tr = ncu_traffic("k_hash_intersect<cover>")
     stages = {k: statistics.mean(r[1][k] for r in res_cover)
-              for k in ("ms_bfs", "ms_cover", "ms_intersect", "ms_total")}
+              for k in ("ms_bfs", "ms_cover", "ms_bucket", "ms_intersect", "ms_main_kernel", "ms_total")}
     stages_plain = {"ms_intersect": ms_kp,
                     "intersect_GBps": plain_bytes / (ms_kp / 1e3) / 1e9,
                     "list_elems": stp["list_elems"]}
@@ -405,7 +405,7 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": units / (ms_e2e_max / 1e3), "unit": "edges/s",
                 "ms_per_step": ms_e2e_max, "h2d_bytes_per_step": csr_bytes,
                 "d2h_bytes_per_step": 8},
-        "roofline": {"bound": "hbm", "kernel": "k_cover_intersect", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "k_hash_intersect<cover>", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "frac_of_8tbs_nominal": achieved / 8000.0,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": ms_k,

@@ -174,6 +174,7 @@ typedef struct {
   int64_t list_elems;         /* sum of list lengths handed to the intersection */
   uint64_t reserved0;
   uint32_t kernel_launches;   /* kernels launched by the call */
+  float ms_main_kernel;       /* the dominant intersection kernel alone */
 } tc_stats_t;
 TC_API int tc_graph_stats(const tc_graph* g, tc_stats_t* out);
 

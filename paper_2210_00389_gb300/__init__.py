@@ -66,7 +66,8 @@ class Stats(ctypes.Structure):
                 ("ms_intersect", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("bfs_levels", ctypes.c_uint32), ("bfs_bottom_up", ctypes.c_uint32),
                 ("edges_intersected", ctypes.c_int64), ("list_elems", ctypes.c_int64),
-                ("reserved0", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint32)]
+                ("reserved0", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint32),
+                ("ms_main_kernel", ctypes.c_float)]
 
 
 class Options(ctypes.Structure):

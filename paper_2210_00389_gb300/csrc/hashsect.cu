@@ -1,0 +1,442 @@
+// Owner-grouped hash intersection: bucketing (a3), intersection with the
+// count-once rule (a4) and reduction (a5) for both the cover path and the
+// plain all-edge path.
+//
+// For an edge (u, v), u < v, the endpoint of larger degree is the "owner" o
+// and the other the "probe" p.  The intersection is counted by probing p's
+// relevant neighbours in a hash table of N(o) (hashing-based intersection,
+// Sec. V-A of Bader et al., "Triangle Counting Through Cover-Edges"; the
+// paper's compute bound for the cover edges, Sec. III, charges expected
+// O(1) per search with a hash table).  The work is then about
+// sum over edges of min(d(u), d(v)) table probes instead of d(u) + d(v)
+// merge steps.
+//
+//   cover: p's level segments (segment.cu): N_{l-1}(p), N_{l+1}(p) and the
+//          same-level ids above v, so every hit satisfies the count-once
+//          rule of Alg. 1 / Thm. 2 (L(w) != l, or L(w) = l and w > v).
+//   plain: p's neighbours above v; every hit is an apex w > v.
+//
+// Bucketing (a3) is a counting sort of the edges by owner.  Owners of degree
+// <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
+// split into work items (owner, slot) of about kItemWork probes; a CTA takes
+// an item, builds a bucketized hash table of N(o) in shared memory (4 slots
+// of 4 bytes per bucket, load <= 1/2, one 16-byte shared load per probe)
+// and probes the item's share of o's edges with one warp per edge.  Rows
+// longer than kWindow are handled in id windows of kWindow consecutive
+// entries; an edge's probe lists are then cut to the window's id range by
+// binary search, so each probe element is looked up once.
+#include "internal.cuh"
+
+namespace tc {
+
+constexpr int kHashThreads = 512;
+constexpr int kHashWarps = kHashThreads / 32;
+constexpr int kHashBuckets = 4096;                // 64 KB of uint4 buckets
+constexpr int64_t kWindow = 2 * kHashBuckets;     // owner entries per table
+constexpr uint32_t kSmallOwner = 64;              // owners this small use the merge
+constexpr unsigned long long kItemWork = 1ull << 19;  // target probes per work item
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+enum { kModeCover = 0, kModePlain = 1 };
+
+struct EdgeSrc {
+  // cover: H pairs + segment data; plain: COO rows + upper starts
+  const uint2* H;
+  const unsigned long long* hoff;
+  const uint4* seg;
+  const uint32_t* scols;
+  const uint32_t* erow;
+  const int64_t* ustart;
+  const int64_t* off;
+  const uint32_t* cols;
+};
+
+// Decode edge `idx`: returns false for plain entries that are not u < v.
+template <int M>
+__device__ __forceinline__ bool edge_at(const EdgeSrc& s, uint64_t idx, uint32_t& u, uint32_t& v) {
+  if (M == kModeCover) {
+    const uint2 e = s.H[idx];
+    u = e.x;
+    v = e.y;
+    return true;
+  } else {
+    u = s.erow[idx];
+    v = s.cols[idx];
+    return u < v;
+  }
+}
+
+__device__ __forceinline__ uint32_t degree(const int64_t* off, uint32_t x) {
+  return (uint32_t)(off[x + 1] - off[x]);
+}
+
+// Owner = endpoint of larger degree (u on ties).
+__device__ __forceinline__ void owner_probe(const int64_t* off, uint32_t u, uint32_t v,
+                                            uint32_t& o, uint32_t& p, uint32_t& dout) {
+  const uint32_t du = degree(off, u), dv = degree(off, v);
+  if (dv > du) { o = v; p = u; dout = dv; } else { o = u; p = v; dout = du; }
+}
+
+// The probe runs of an edge: up to three (pointer, length) pairs.
+struct Runs {
+  const uint32_t* ptr[3];
+  uint32_t len[3];
+  int n;
+};
+
+template <int M>
+__device__ __forceinline__ void probe_runs(const EdgeSrc& s, uint64_t idx, uint32_t u, uint32_t v,
+                                           uint32_t p, Runs& r) {
+  if (M == kModeCover) {
+    const int64_t op = s.off[p], ep = s.off[p + 1];
+    const uint4 sg = s.seg[p];
+    // same-level ids of p above v: for p = v the run starts at sg.y; for
+    // p = u, v is entry (idx - hoff[u]) of u's run above u
+    const uint32_t cut = (p == v) ? sg.y : sg.y + (uint32_t)(idx - s.hoff[u]) + 1u;
+    r.ptr[0] = s.scols + op;           r.len[0] = sg.x;
+    r.ptr[1] = s.scols + op + cut;     r.len[1] = sg.z - cut;
+    r.ptr[2] = s.scols + op + sg.z;    r.len[2] = (uint32_t)(ep - op) - sg.z;
+    r.n = 3;
+  } else {
+    int64_t b;
+    if (p == u) b = (int64_t)idx + 1;  // entries of u after v
+    else b = s.ustart[v];
+    r.ptr[0] = s.cols + b;
+    r.len[0] = (uint32_t)(s.off[p + 1] - b);
+    r.n = 1;
+  }
+}
+
+// ------------------------------------------------------------------ bucketing
+
+// Per edge: owners of degree <= kSmallOwner go to the small list, others
+// are counted per owner with their probe work.
+template <int M>
+__global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ owner_cnt,
+                               unsigned long long* __restrict__ owner_work,
+                               uint32_t* __restrict__ small_list, unsigned long long* ctrl) {
+  const int lane = threadIdx.x & 31;
+  uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (; base < nidx; base += stride) {
+    const uint64_t idx = base + lane;
+    bool small = false;
+    if (idx < nidx) {
+      uint32_t u, v;
+      if (edge_at<M>(s, idx, u, v)) {
+        uint32_t o, p, dout;
+        owner_probe(s.off, u, v, o, p, dout);
+        if (dout <= kSmallOwner) {
+          small = true;
+        } else {
+          Runs r;
+          probe_runs<M>(s, idx, u, v, p, r);
+          unsigned long long w = 0;
+          for (int k = 0; k < r.n; ++k) w += r.len[k];
+          atomicAdd(&owner_cnt[o], 1u);
+          atomicAdd(&owner_work[o], w + 1);
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, small);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long b0 = 0;
+      if (lane == leader) b0 = atomicAdd(&ctrl[kCtrlQ0], (unsigned long long)__popc(m));
+      b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
+      if (small) small_list[b0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
+    }
+  }
+}
+
+template <int M>
+__global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long long* __restrict__ ostart,
+                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ tasks) {
+  uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (; idx < nidx; idx += stride) {
+    uint32_t u, v;
+    if (!edge_at<M>(s, idx, u, v)) continue;
+    uint32_t o, p, dout;
+    owner_probe(s.off, u, v, o, p, dout);
+    if (dout <= kSmallOwner) continue;
+    const uint32_t k = atomicAdd(&cursor[o], 1u);
+    tasks[ostart[o] + k] = (uint32_t)idx;
+  }
+}
+
+// Slots per owner: about kItemWork probes per item, and at least 4 probes
+// per table entry built (each item rebuilds N(o)'s table).
+__device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long work, uint32_t d) {
+  if (cnt == 0) return 0;
+  unsigned long long s1 = (work + kItemWork - 1) / kItemWork;
+  unsigned long long s2 = work / (4ull * d);
+  unsigned long long s = s1 < s2 ? s1 : s2;
+  const unsigned long long cap = (cnt + 3) / 4;
+  if (s > cap) s = cap;
+  if (s < 1) s = 1;
+  if (s > 65535) s = 65535;
+  return (uint32_t)s;
+}
+
+__global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
+                              const uint32_t* __restrict__ owner_cnt,
+                              const unsigned long long* __restrict__ owner_work,
+                              unsigned long long* __restrict__ nslots) {
+  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; o < (int64_t)n; o += stride)
+    nslots[o] = owner_slots(owner_cnt[o], owner_work[o], degree(off, (uint32_t)o));
+}
+
+// items[k] = (owner, slot << 16 | slots)
+__global__ void k_item_write(const int64_t* __restrict__ off, uint32_t n,
+                             const uint32_t* __restrict__ owner_cnt,
+                             const unsigned long long* __restrict__ owner_work,
+                             const unsigned long long* __restrict__ item_start,
+                             uint2* __restrict__ items) {
+  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; o < (int64_t)n; o += stride) {
+    const uint32_t s = owner_slots(owner_cnt[o], owner_work[o], degree(off, (uint32_t)o));
+    const unsigned long long b = item_start[o];
+    for (uint32_t k = 0; k < s; ++k) items[b + k] = make_uint2((uint32_t)o, (k << 16) | s);
+  }
+}
+
+__global__ void k_u32_to_u64(const uint32_t* __restrict__ a, uint32_t n, unsigned long long* b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < (int64_t)n; i += stride) b[i] = a[i];
+}
+
+// ------------------------------------------------------------------ hashing
+
+// Fibonacci hashing: the top log2(buckets) bits of w * 2^32/phi.
+__device__ __forceinline__ uint32_t hash_bucket(uint32_t w, uint32_t shift) {
+  return (w * 0x9E3779B1u) >> shift;
+}
+
+__device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t shift, uint32_t mask,
+                                             uint32_t w) {
+  uint32_t b = hash_bucket(w, shift);
+  while (true) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (atomicCAS(&tab[4 * b + k], kEmpty, w) == kEmpty) return;
+    b = (b + 1) & mask;
+  }
+}
+
+__device__ __forceinline__ bool table_find(const uint4* tab4, uint32_t shift, uint32_t mask,
+                                           uint32_t w) {
+  uint32_t b = hash_bucket(w, shift);
+  while (true) {
+    const uint4 q = tab4[b];
+    if (q.x == w || q.y == w || q.z == w || q.w == w) return true;
+    if (q.w == kEmpty) return false;  // slots fill in order, so the bucket had room
+    b = (b + 1) & mask;
+  }
+}
+
+// lower_bound over a sorted run (one lane)
+__device__ __forceinline__ uint32_t lb32(const uint32_t* a, uint32_t len, uint32_t x) {
+  uint32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+template <int M>
+__global__ void __launch_bounds__(kHashThreads, 3)
+k_hash_intersect(EdgeSrc s, const uint2* __restrict__ items, uint64_t nitems,
+                 const unsigned long long* __restrict__ ostart,
+                 const uint32_t* __restrict__ owner_cnt, const uint32_t* __restrict__ tasks,
+                 uint32_t* __restrict__ per_edge, unsigned long long* item_counter,
+                 unsigned long long* ctrl) {
+  extern __shared__ uint4 tab4[];  // kHashBuckets buckets (dynamic shared memory)
+  __shared__ unsigned long long s_item;
+  uint32_t* tab = reinterpret_cast<uint32_t*>(tab4);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long acc = 0, probes = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(item_counter, 1ull);
+    __syncthreads();
+    const unsigned long long it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const uint2 item = items[it];
+    const uint32_t o = item.x, slot = item.y >> 16, nsl = item.y & 0xFFFFu;
+    const uint64_t T0 = ostart[o], T = owner_cnt[o];
+    const uint64_t ta = T0 + T * slot / nsl, tb = T0 + T * (slot + 1) / nsl;
+    const int64_t ro = s.off[o];
+    const uint32_t d = (uint32_t)(s.off[o + 1] - ro);
+    const uint32_t nwin = (uint32_t)((d + kWindow - 1) / kWindow);
+    uint32_t nb = kHashBuckets;
+    if (nwin == 1) {
+      nb = 32;
+      while (nb * 2 < d) nb <<= 1;  // >= 2 slots per entry
+    }
+    const uint32_t mask = nb - 1;
+    const uint32_t shift = 32u - (uint32_t)(__ffs(nb) - 1);
+    for (uint32_t wdx = 0; wdx < nwin; ++wdx) {
+      const uint32_t wb = wdx * (uint32_t)kWindow;
+      const uint32_t we = min(d, wb + (uint32_t)kWindow);
+      const uint32_t lo = s.cols[ro + wb], hi = s.cols[ro + we - 1];
+      for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x)
+        tab4[k] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+      __syncthreads();
+      for (uint32_t k = wb + threadIdx.x; k < we; k += blockDim.x)
+        table_insert(tab, shift, mask, s.cols[ro + k]);
+      __syncthreads();
+      for (uint64_t t = ta + wid; t < tb; t += kHashWarps) {
+        const uint32_t idx = tasks[t];
+        uint32_t u, v;
+        edge_at<M>(s, idx, u, v);
+        const uint32_t p = (o == u) ? v : u;
+        Runs r;
+        probe_runs<M>(s, idx, u, v, p, r);
+        unsigned c = 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q >= r.n) break;
+          const uint32_t* run = r.ptr[q];
+          uint32_t a = 0, bnd = r.len[q];
+          if (nwin > 1) {  // cut the run to the window's id range
+            uint32_t x = 0;
+            if (lane == 0) x = lb32(run, bnd, lo);
+            else if (lane == 1) x = lb32(run, bnd, hi + 1u);
+            a = __shfl_sync(0xFFFFFFFFu, x, 0);
+            bnd = __shfl_sync(0xFFFFFFFFu, x, 1);
+          }
+          for (uint32_t k = a + lane; k < bnd; k += 32) c += table_find(tab4, shift, mask, run[k]);
+          if (lane == 0) probes += bnd - a;
+        }
+        acc += c;
+        if (per_edge) {
+          const unsigned long long tsum = warp_sum_u64(c);
+          if (lane == 0 && tsum) atomicAdd(&per_edge[idx], (uint32_t)tsum);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // block reduction of the count and the probe total
+  __shared__ unsigned long long red[2][kHashWarps];
+  acc = warp_sum_u64(acc);
+  probes = warp_sum_u64(probes);
+  if (lane == 0) { red[0][wid] = acc; red[1][wid] = probes; }
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long a = lane < kHashWarps ? red[0][lane] : 0ull;
+    unsigned long long b = lane < kHashWarps ? red[1][lane] : 0ull;
+    a = warp_sum_u64(a);
+    b = warp_sum_u64(b);
+    if (lane == 0) {
+      if (a) atomicAdd(&ctrl[kCtrlCount], a);
+      if (b) atomicAdd(&ctrl[kCtrlElems], b);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ driver
+
+// defined in intersect.cu: warp merge over a list of edge indices
+int merge_small_edges(tc_graph* g, int mode, const uint32_t* list, uint64_t nlist,
+                      const int64_t* ustart, uint32_t* per_edge);
+
+int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge) {
+  cudaStream_t st = g->stream;
+  const int T = 256;
+  EdgeSrc s{};
+  s.off = g->off;
+  s.cols = g->cols;
+  uint64_t nidx;
+  if (mode == kModeCover) {
+    s.H = g->cover.p;
+    s.hoff = g->hoff.p;
+    s.seg = g->seg.p;
+    s.scols = g->scols.p;
+    nidx = (uint64_t)g->num_cover;
+  } else {
+    s.erow = g->erow.p;
+    s.ustart = ustart;
+    nidx = (uint64_t)g->nnz;
+  }
+  if (nidx == 0) return TC_OK;
+  DevBuf<uint32_t> owner_cnt, cursor, small_list, tasks;
+  DevBuf<unsigned long long> owner_work, ostart, nslots;
+  DevBuf<uint2> items;
+  TC_TRY(owner_cnt.alloc(g->n, st));
+  TC_TRY(cursor.alloc(g->n, st));
+  TC_TRY(owner_work.alloc(g->n, st));
+  TC_TRY(ostart.alloc(g->n, st));
+  TC_TRY(nslots.alloc(g->n, st));
+  TC_TRY(small_list.alloc(nidx, st));
+  TC_CUDA(cudaMemsetAsync(owner_cnt.p, 0, sizeof(uint32_t) * g->n, st));
+  TC_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(uint32_t) * g->n, st));
+  TC_CUDA(cudaMemsetAsync(owner_work.p, 0, sizeof(unsigned long long) * g->n, st));
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlQ0, 0, sizeof(unsigned long long), st));
+  if (mode == kModeCover)
+    launch(k_bucket_count<kModeCover>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx,
+           owner_cnt.p, owner_work.p, small_list.p, g->ctrl.p);
+  else
+    launch(k_bucket_count<kModePlain>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx,
+           owner_cnt.p, owner_work.p, small_list.p, g->ctrl.p);
+  launch(k_u32_to_u64, grid_for(g->n, T), T, 0, st, owner_cnt.p, g->n, ostart.p);
+  TC_TRY(exclusive_scan_u64(ostart.p, g->n, g->ctrl.p + kCtrlTmp, st));
+  launch(k_item_counts, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
+         nslots.p);
+  TC_TRY(exclusive_scan_u64(nslots.p, g->n, g->ctrl.p + kCtrlQ1, st));
+  TC_CUDA(cudaGetLastError());
+  TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, st));
+  TC_CUDA(cudaStreamSynchronize(st));
+  const uint64_t nsmall = g->ctrl_host[kCtrlQ0];
+  const uint64_t ntasks = g->ctrl_host[kCtrlTmp];
+  const uint64_t nitems = g->ctrl_host[kCtrlQ1];
+  TC_TRY(tasks.alloc(ntasks, st));
+  TC_TRY(items.alloc(nitems, st));
+  if (ntasks > 0) {
+    if (mode == kModeCover)
+      launch(k_bucket_scatter<kModeCover>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p,
+             cursor.p, tasks.p);
+    else
+      launch(k_bucket_scatter<kModePlain>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p,
+             cursor.p, tasks.p);
+    launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
+           nslots.p, items.p);
+  }
+  TC_CUDA(cudaGetLastError());
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), st));
+  cudaEventRecord(g->ev[6], st);  // end of bucketing
+  if (nitems > 0) {
+    const int grid = sm_count() * 3;
+    const size_t smem = sizeof(uint4) * kHashBuckets;
+    if (mode == kModeCover) {
+      TC_CUDA(cudaFuncSetAttribute(k_hash_intersect<kModeCover>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      launch(k_hash_intersect<kModeCover>, grid, kHashThreads, smem, st, s, items.p, nitems,
+             ostart.p, owner_cnt.p, tasks.p, per_edge, g->ctrl.p + kCtrlWork, g->ctrl.p);
+    } else {
+      TC_CUDA(cudaFuncSetAttribute(k_hash_intersect<kModePlain>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      launch(k_hash_intersect<kModePlain>, grid, kHashThreads, smem, st, s, items.p, nitems,
+             ostart.p, owner_cnt.p, tasks.p, per_edge, g->ctrl.p + kCtrlWork, g->ctrl.p);
+    }
+    TC_CUDA(cudaGetLastError());
+  }
+  cudaEventRecord(g->ev[7], st);  // end of the hash kernel
+  if (nsmall > 0)
+    TC_TRY(merge_small_edges(g, mode, small_list.p, nsmall, ustart, per_edge));
+  return TC_OK;
+}
+
+}  // namespace tc

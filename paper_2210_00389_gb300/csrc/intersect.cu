@@ -106,7 +106,35 @@ __device__ __forceinline__ unsigned warp_intersect(const uint32_t* __restrict__ 
   return cnt;
 }
 
-// Cover edges, warp per edge, chunks grabbed from *work.
+// One cover edge i = (u, v) by segment-wise warp merges; returns the lane's
+// share of c_uv and adds the list lengths streamed to *elems (lane 0).
+__device__ __forceinline__ unsigned cover_edge_merge(int64_t i, const uint2* __restrict__ H,
+                                                     const int64_t* __restrict__ off,
+                                                     const uint32_t* __restrict__ scols,
+                                                     const uint4* __restrict__ seg,
+                                                     const unsigned long long* __restrict__ hoff,
+                                                     unsigned long long* elems) {
+  const int lane = threadIdx.x & 31;
+  const uint2 e = H[i];
+  const int64_t ou = off[e.x], eu = off[e.x + 1];
+  const int64_t ov = off[e.y], ev = off[e.y + 1];
+  const uint4 su = seg[e.x], sv = seg[e.y];
+  const uint32_t* Ru = scols + ou;
+  const uint32_t* Rv = scols + ov;
+  // v is entry (i - hoff[u]) of u's same-level run above u, so the
+  // same-level ids of u greater than v start right after it
+  const uint32_t cut = su.y + (uint32_t)(i - (int64_t)hoff[e.x]) + 1u;
+  unsigned c = warp_intersect(Ru, su.x, Rv, sv.x);                      // level l-1
+  c += warp_intersect(Ru + cut, su.z - cut, Rv + sv.y, sv.z - sv.y);    // level l, > v
+  c += warp_intersect(Ru + su.z, (eu - ou) - su.z, Rv + sv.z, (ev - ov) - sv.z);  // l+1
+  if (lane == 0)
+    *elems += (unsigned long long)(su.x + sv.x + (su.z - cut) + (sv.z - sv.y)) +
+              (unsigned long long)((eu - ou) - su.z + (ev - ov) - sv.z);
+  return c;
+}
+
+// Cover edges, warp per edge, chunks grabbed from *work (merge-only path,
+// used when the edge count does not fit the 32-bit task lists).
 __global__ void __launch_bounds__(kIsThreads)
 k_cover_intersect(const uint2* __restrict__ H, int64_t nh, const int64_t* __restrict__ off,
                   const uint32_t* __restrict__ scols, const uint4* __restrict__ seg,
@@ -122,22 +150,8 @@ k_cover_intersect(const uint2* __restrict__ H, int64_t nh, const int64_t* __rest
     if ((int64_t)base >= nh) break;
     const int64_t end = min((int64_t)base + kCoverChunk, nh);
     for (int64_t i = (int64_t)base; i < end; ++i) {
-      const uint2 e = H[i];
-      const int64_t ou = off[e.x], eu = off[e.x + 1];
-      const int64_t ov = off[e.y], ev = off[e.y + 1];
-      const uint4 su = seg[e.x], sv = seg[e.y];
-      const uint32_t* Ru = scols + ou;
-      const uint32_t* Rv = scols + ov;
-      // v is entry (i - hoff[u]) of u's same-level run above u, so the
-      // same-level ids of u greater than v start right after it
-      const uint32_t cut = su.y + (uint32_t)(i - (int64_t)hoff[e.x]) + 1u;
-      unsigned c = warp_intersect(Ru, su.x, Rv, sv.x);                      // level l-1
-      c += warp_intersect(Ru + cut, su.z - cut, Rv + sv.y, sv.z - sv.y);    // level l, > v
-      c += warp_intersect(Ru + su.z, (eu - ou) - su.z, Rv + sv.z, (ev - ov) - sv.z);  // l+1
+      const unsigned c = cover_edge_merge(i, H, off, scols, seg, hoff, &elems);
       acc += c;
-      if (lane == 0)
-        elems += (unsigned long long)(su.x + sv.x + (su.z - cut) + (sv.z - sv.y)) +
-                 (unsigned long long)((eu - ou) - su.z + (ev - ov) - sv.z);
       if (per_edge) {
         const unsigned long long t = warp_sum(c);
         if (lane == 0) per_edge[i] = (uint32_t)t;
@@ -147,6 +161,60 @@ k_cover_intersect(const uint2* __restrict__ H, int64_t nh, const int64_t* __rest
   block_add(acc, &ctrl[kCtrlCount]);
   __syncthreads();
   block_add(elems, &ctrl[kCtrlElems]);
+}
+
+// Edges listed by the bucketing step as having a small owner (both
+// endpoints of degree <= the small-owner bound): warp merge, list chunks
+// grabbed from *work.  mode 0 = cover (list holds H indices), 1 = plain
+// (list holds CSR entry indices with u < v).
+__global__ void __launch_bounds__(kIsThreads)
+k_small_merge(int mode, const uint32_t* __restrict__ list, int64_t nlist,
+              const uint2* __restrict__ H, const int64_t* __restrict__ off,
+              const uint32_t* __restrict__ scols, const uint4* __restrict__ seg,
+              const unsigned long long* __restrict__ hoff, const uint32_t* __restrict__ erow,
+              const uint32_t* __restrict__ cols, const int64_t* __restrict__ ustart,
+              uint32_t* __restrict__ per_edge, unsigned long long* work, unsigned long long* ctrl) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long acc = 0, elems = 0;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(work, (unsigned long long)kPlainChunk);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if ((int64_t)base >= nlist) break;
+    const int64_t end = min((int64_t)base + kPlainChunk, nlist);
+    for (int64_t j = (int64_t)base; j < end; ++j) {
+      const int64_t i = list[j];
+      unsigned c;
+      if (mode == 0) {
+        c = cover_edge_merge(i, H, off, scols, seg, hoff, &elems);
+        if (per_edge) {
+          const unsigned long long t = warp_sum(c);
+          if (lane == 0) per_edge[i] = (uint32_t)t;
+        }
+      } else {
+        const uint32_t u = erow[i], v = cols[i];
+        const int64_t au = i + 1, bv = ustart[v];
+        const int64_t la = off[u + 1] - au, lb = off[v + 1] - bv;
+        c = warp_intersect(cols + au, la, cols + bv, lb);
+        if (lane == 0) elems += (unsigned long long)(la + lb);
+      }
+      acc += c;
+    }
+  }
+  block_add(acc, &ctrl[kCtrlCount]);
+  __syncthreads();
+  block_add(elems, &ctrl[kCtrlElems]);
+}
+
+int merge_small_edges(tc_graph* g, int mode, const uint32_t* list, uint64_t nlist,
+                      const int64_t* ustart, uint32_t* per_edge) {
+  cudaStream_t s = g->stream;
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
+  launch(k_small_merge, grid_for((int64_t)nlist * 32, kIsThreads, 8), kIsThreads, 0, s, mode, list,
+         (int64_t)nlist, g->cover.p, g->off, g->scols.p, g->seg.p, g->hoff.p, g->erow.p, g->cols,
+         ustart, per_edge, g->ctrl.p + kCtrlWork, g->ctrl.p);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
 }
 
 // ustart[v] = index (into cols) of the first neighbour of v greater than v.
@@ -191,14 +259,38 @@ k_plain_intersect(const uint32_t* __restrict__ erow, int64_t nnz, const int64_t*
   block_add(elems, &ctrl[kCtrlElems]);
 }
 
+int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge);
+
+// Stage timings: ev4 -> ev6 bucketing, ev6 -> ev7 hash kernel, ev7 -> ev5
+// small-owner merge (the merge-only fallback records ev6 = ev7 = ev4).
+static void finish_stats(tc_graph* g, bool hashed) {
+  tc_stats_t& st = g->stats;
+  st.list_elems = (int64_t)g->ctrl_host[kCtrlElems];
+  st.ms_bucket = 0.f;
+  if (hashed) {
+    cudaEventElapsedTime(&st.ms_bucket, g->ev[4], g->ev[6]);
+    cudaEventElapsedTime(&st.ms_main_kernel, g->ev[6], g->ev[7]);
+    cudaEventElapsedTime(&st.ms_intersect, g->ev[6], g->ev[5]);
+  } else {
+    cudaEventElapsedTime(&st.ms_main_kernel, g->ev[4], g->ev[5]);
+    st.ms_intersect = st.ms_main_kernel;
+  }
+  cudaGetLastError();  // a timing query that failed must not leak into later checks
+}
+
 int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
   cudaStream_t s = g->stream;
   if (g->num_cover < 0) TC_TRY(compute_cover(g));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
+  if (per_edge_out && g->num_cover > 0)
+    TC_CUDA(cudaMemsetAsync(per_edge_out, 0, sizeof(uint32_t) * (size_t)g->num_cover, s));
+  const bool hashed = g->num_cover < (int64_t)0xFFFFFFFFll;
   cudaEventRecord(g->ev[4], s);
-  if (g->num_cover > 0) {
+  if (hashed) {
+    TC_TRY(hash_count(g, 0, nullptr, per_edge_out));
+  } else {
     launch(k_cover_intersect, grid_for(g->num_cover * 32, kIsThreads, 8), kIsThreads, 0, s,
            g->cover.p, g->num_cover, g->off, g->scols.p, g->seg.p, g->hoff.p, per_edge_out,
            g->ctrl.p + kCtrlWork, g->ctrl.p);
@@ -210,8 +302,7 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
   TC_CUDA(cudaStreamSynchronize(s));
   *total = g->ctrl_host[kCtrlCount];
   g->stats.edges_intersected = g->num_cover;
-  g->stats.list_elems = (int64_t)g->ctrl_host[kCtrlElems];
-  cudaEventElapsedTime(&g->stats.ms_intersect, g->ev[4], g->ev[5]);
+  finish_stats(g, hashed && g->num_cover > 0);
   return TC_OK;
 }
 
@@ -220,16 +311,21 @@ int count_plain(tc_graph* g, uint64_t* total) {
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
-  g->stats.ms_intersect = 0.f;
+  g->stats.ms_intersect = g->stats.ms_bucket = g->stats.ms_main_kernel = 0.f;
+  const bool hashed = g->nnz < (int64_t)0xFFFFFFFFll;
+  DevBuf<int64_t> ustart;
   if (g->nnz > 0) {
-    DevBuf<int64_t> ustart;
     TC_TRY(ustart.alloc(g->n, s));
     launch(k_upper_start, grid_for(g->n, kIsThreads), kIsThreads, 0, s, g->off, g->cols, g->n,
            ustart.p);
     cudaEventRecord(g->ev[4], s);
-    launch(k_plain_intersect, grid_for(g->nnz * 32, kIsThreads, 8), kIsThreads, 0, s, g->erow.p,
-           g->nnz, g->off, g->cols, ustart.p, g->ctrl.p + kCtrlWork, g->ctrl.p);
-    TC_CUDA(cudaGetLastError());
+    if (hashed) {
+      TC_TRY(hash_count(g, 1, ustart.p, nullptr));
+    } else {
+      launch(k_plain_intersect, grid_for(g->nnz * 32, kIsThreads, 8), kIsThreads, 0, s, g->erow.p,
+             g->nnz, g->off, g->cols, ustart.p, g->ctrl.p + kCtrlWork, g->ctrl.p);
+      TC_CUDA(cudaGetLastError());
+    }
     cudaEventRecord(g->ev[5], s);
   }
   TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
@@ -237,8 +333,7 @@ int count_plain(tc_graph* g, uint64_t* total) {
   TC_CUDA(cudaStreamSynchronize(s));
   *total = g->ctrl_host[kCtrlCount];
   g->stats.edges_intersected = g->nnz / 2;
-  g->stats.list_elems = (int64_t)g->ctrl_host[kCtrlElems];
-  if (g->nnz > 0) cudaEventElapsedTime(&g->stats.ms_intersect, g->ev[4], g->ev[5]);
+  if (g->nnz > 0) finish_stats(g, hashed);
   return TC_OK;
 }
 

@@ -3,28 +3,34 @@
 // plain all-edge path.
 //
 // For an edge (u, v), u < v, the endpoint of larger degree is the "owner" o
-// and the other the "probe" p.  The intersection is counted by probing p's
-// relevant neighbours in a hash table of N(o) (hashing-based intersection,
-// Sec. V-A of Bader et al., "Triangle Counting Through Cover-Edges"; the
-// paper's compute bound for the cover edges, Sec. III, charges expected
-// O(1) per search with a hash table).  The work is then about
-// sum over edges of min(d(u), d(v)) table probes instead of d(u) + d(v)
-// merge steps.
+// and the other the "probe" p.  The intersection is counted by looking up
+// p's relevant neighbours in a hash table of N(o) (hashing-based
+// intersection, Sec. V-A of Bader et al., "Triangle Counting Through
+// Cover-Edges"; the paper's compute bound for the cover edges, Sec. III,
+// charges expected O(1) per search with a hash table).  The work is about
+// sum over edges of min(d(u), d(v)) lookups instead of d(u) + d(v) merge
+// steps.
 //
-//   cover: p's level segments (segment.cu): N_{l-1}(p), N_{l+1}(p) and the
-//          same-level ids above v, so every hit satisfies the count-once
+//   cover: p's level segments (segment.cu) N_{l-1}(p), the same-level ids
+//          above v and N_{l+1}(p), so every hit satisfies the count-once
 //          rule of Alg. 1 / Thm. 2 (L(w) != l, or L(w) = l and w > v).
 //   plain: p's neighbours above v; every hit is an apex w > v.
 //
+// In both cases the probe elements form at most two contiguous runs of one
+// row array, R1 = [base, base + x) and R2 = [base + cut, base + end)
+// (cover: R1 = level l-1, R2 = same level above v followed by level l+1,
+// which are adjacent in the segmented row), stored as a 16-byte descriptor
+// per edge by the bucketing step.
+//
 // Bucketing (a3) is a counting sort of the edges by owner.  Owners of degree
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
-// split into work items (owner, slot) of about kItemWork probes; a CTA takes
-// an item, builds a bucketized hash table of N(o) in shared memory (4 slots
-// of 4 bytes per bucket, load <= 1/2, one 16-byte shared load per probe)
-// and probes the item's share of o's edges with one warp per edge.  Rows
-// longer than kWindow are handled in id windows of kWindow consecutive
-// entries; an edge's probe lists are then cut to the window's id range by
-// binary search, so each probe element is looked up once.
+// split into work items (owner, slot) of about kItemWork lookups; a CTA
+// takes an item, builds a bucketized hash table of N(o) in shared memory
+// (4 slots of 4 bytes per bucket, load <= 1/2, one 16-byte shared load per
+// lookup) and its warps take the item's edges from a shared counter.  Rows
+// longer than kWindow are processed in windows of kWindow consecutive
+// entries (an id range); every probe run keeps a cursor across windows, so
+// each probe element is looked up once.
 #include "internal.cuh"
 
 namespace tc {
@@ -32,9 +38,9 @@ namespace tc {
 constexpr int kHashThreads = 512;
 constexpr int kHashWarps = kHashThreads / 32;
 constexpr int kHashBuckets = 4096;                // 64 KB of uint4 buckets
-constexpr int64_t kWindow = 2 * kHashBuckets;     // owner entries per table
+constexpr uint32_t kWindow = 2 * kHashBuckets;    // owner entries per table
 constexpr uint32_t kSmallOwner = 64;              // owners this small use the merge
-constexpr unsigned long long kItemWork = 1ull << 19;  // target probes per work item
+constexpr unsigned long long kItemWork = 1ull << 19;  // target lookups per work item
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 enum { kModeCover = 0, kModePlain = 1 };
@@ -44,7 +50,6 @@ struct EdgeSrc {
   const uint2* H;
   const unsigned long long* hoff;
   const uint4* seg;
-  const uint32_t* scols;
   const uint32_t* erow;
   const int64_t* ustart;
   const int64_t* off;
@@ -77,40 +82,32 @@ __device__ __forceinline__ void owner_probe(const int64_t* off, uint32_t u, uint
   if (dv > du) { o = v; p = u; dout = dv; } else { o = u; p = v; dout = du; }
 }
 
-// The probe runs of an edge: up to three (pointer, length) pairs.
-struct Runs {
-  const uint32_t* ptr[3];
-  uint32_t len[3];
-  int n;
-};
-
+// Probe descriptor {base, x, cut, end}: runs [base, base+x) and
+// [base+cut, base+end) of the probe row array (scols for cover, cols for
+// plain).
 template <int M>
-__device__ __forceinline__ void probe_runs(const EdgeSrc& s, uint64_t idx, uint32_t u, uint32_t v,
-                                           uint32_t p, Runs& r) {
+__device__ __forceinline__ uint4 probe_desc(const EdgeSrc& s, uint64_t idx, uint32_t u, uint32_t v,
+                                            uint32_t p) {
   if (M == kModeCover) {
-    const int64_t op = s.off[p], ep = s.off[p + 1];
+    const int64_t op = s.off[p];
+    const uint32_t dp = (uint32_t)(s.off[p + 1] - op);
     const uint4 sg = s.seg[p];
     // same-level ids of p above v: for p = v the run starts at sg.y; for
     // p = u, v is entry (idx - hoff[u]) of u's run above u
     const uint32_t cut = (p == v) ? sg.y : sg.y + (uint32_t)(idx - s.hoff[u]) + 1u;
-    r.ptr[0] = s.scols + op;           r.len[0] = sg.x;
-    r.ptr[1] = s.scols + op + cut;     r.len[1] = sg.z - cut;
-    r.ptr[2] = s.scols + op + sg.z;    r.len[2] = (uint32_t)(ep - op) - sg.z;
-    r.n = 3;
+    return make_uint4((uint32_t)op, sg.x, cut, dp);
   } else {
-    int64_t b;
-    if (p == u) b = (int64_t)idx + 1;  // entries of u after v
-    else b = s.ustart[v];
-    r.ptr[0] = s.cols + b;
-    r.len[0] = (uint32_t)(s.off[p + 1] - b);
-    r.n = 1;
+    const int64_t b = (p == u) ? (int64_t)idx + 1 : s.ustart[v];  // neighbours of p above v
+    return make_uint4((uint32_t)b, 0u, 0u, (uint32_t)(s.off[p + 1] - b));
   }
 }
+
+__device__ __forceinline__ uint32_t desc_work(uint4 d) { return d.y + (d.w - d.z); }
 
 // ------------------------------------------------------------------ bucketing
 
 // Per edge: owners of degree <= kSmallOwner go to the small list, others
-// are counted per owner with their probe work.
+// are counted per owner with their lookup work.
 template <int M>
 __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ owner_cnt,
                                unsigned long long* __restrict__ owner_work,
@@ -129,12 +126,9 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
         if (dout <= kSmallOwner) {
           small = true;
         } else {
-          Runs r;
-          probe_runs<M>(s, idx, u, v, p, r);
-          unsigned long long w = 0;
-          for (int k = 0; k < r.n; ++k) w += r.len[k];
+          const uint4 d = probe_desc<M>(s, idx, u, v, p);
           atomicAdd(&owner_cnt[o], 1u);
-          atomicAdd(&owner_work[o], w + 1);
+          atomicAdd(&owner_work[o], (unsigned long long)desc_work(d) + 1ull);
         }
       }
     }
@@ -149,9 +143,12 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
   }
 }
 
+// Scatter every non-small edge's descriptor (and its index, for per-edge
+// counts) into its owner's task range.
 template <int M>
 __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long long* __restrict__ ostart,
-                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ tasks) {
+                                 uint32_t* __restrict__ cursor, uint4* __restrict__ descs,
+                                 uint32_t* __restrict__ task_idx) {
   uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (; idx < nidx; idx += stride) {
@@ -160,17 +157,18 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
     uint32_t o, p, dout;
     owner_probe(s.off, u, v, o, p, dout);
     if (dout <= kSmallOwner) continue;
-    const uint32_t k = atomicAdd(&cursor[o], 1u);
-    tasks[ostart[o] + k] = (uint32_t)idx;
+    const unsigned long long t = ostart[o] + atomicAdd(&cursor[o], 1u);
+    descs[t] = probe_desc<M>(s, idx, u, v, p);
+    if (task_idx) task_idx[t] = (uint32_t)idx;
   }
 }
 
-// Slots per owner: about kItemWork probes per item, and at least 4 probes
-// per table entry built (each item rebuilds N(o)'s table).
+// Slots per owner: about kItemWork lookups per item, and at least 4 lookups
+// per table entry built (each item builds N(o)'s table).
 __device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long work, uint32_t d) {
   if (cnt == 0) return 0;
-  unsigned long long s1 = (work + kItemWork - 1) / kItemWork;
-  unsigned long long s2 = work / (4ull * d);
+  const unsigned long long s1 = (work + kItemWork - 1) / kItemWork;
+  const unsigned long long s2 = work / (4ull * d);
   unsigned long long s = s1 < s2 ? s1 : s2;
   const unsigned long long cap = (cnt + 3) / 4;
   if (s > cap) s = cap;
@@ -228,25 +226,17 @@ __device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t shift, uint
   }
 }
 
-__device__ __forceinline__ bool table_find(const uint4* tab4, uint32_t shift, uint32_t mask,
-                                           uint32_t w) {
+// Slots of a bucket fill in order and never empty again, so a bucket whose
+// last slot is empty ends the search.
+__device__ __forceinline__ unsigned table_find(const uint4* tab4, uint32_t shift, uint32_t mask,
+                                               uint32_t w) {
   uint32_t b = hash_bucket(w, shift);
   while (true) {
     const uint4 q = tab4[b];
-    if (q.x == w || q.y == w || q.z == w || q.w == w) return true;
-    if (q.w == kEmpty) return false;  // slots fill in order, so the bucket had room
+    if (q.x == w || q.y == w || q.z == w || q.w == w) return 1u;
+    if (q.w == kEmpty) return 0u;
     b = (b + 1) & mask;
   }
-}
-
-// lower_bound over a sorted run (one lane)
-__device__ __forceinline__ uint32_t lb32(const uint32_t* a, uint32_t len, uint32_t x) {
-  uint32_t lo = 0, hi = len;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
@@ -254,15 +244,38 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
   return x;
 }
 
+// Look up P[pos..end) while the elements are <= hi; returns the lane's hits
+// and advances pos past the elements looked up.
+__device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict__ P, uint32_t& pos,
+                                                     uint32_t end, uint32_t hi, const uint4* tab4,
+                                                     uint32_t shift, uint32_t mask) {
+  const int lane = threadIdx.x & 31;
+  unsigned c = 0;
+  while (pos < end) {
+    const uint32_t k = pos + lane;
+    const bool valid = k < end;
+    const uint32_t w = valid ? __ldg(P + k) : kEmpty;
+    const bool in = valid && w <= hi;
+    if (in) c += table_find(tab4, shift, mask, w);
+    const uint32_t nin = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in));
+    pos += nin;  // the elements <= hi form a prefix (runs are sorted)
+    if (nin < 32) break;
+  }
+  return c;
+}
+
 template <int M>
 __global__ void __launch_bounds__(kHashThreads, 3)
-k_hash_intersect(EdgeSrc s, const uint2* __restrict__ items, uint64_t nitems,
-                 const unsigned long long* __restrict__ ostart,
-                 const uint32_t* __restrict__ owner_cnt, const uint32_t* __restrict__ tasks,
+k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
+                 const uint32_t* __restrict__ pcols, const uint2* __restrict__ items,
+                 uint64_t nitems, const unsigned long long* __restrict__ ostart,
+                 const uint32_t* __restrict__ owner_cnt, const uint4* __restrict__ descs,
+                 const uint32_t* __restrict__ task_idx, uint2* __restrict__ cursors,
                  uint32_t* __restrict__ per_edge, unsigned long long* item_counter,
                  unsigned long long* ctrl) {
   extern __shared__ uint4 tab4[];  // kHashBuckets buckets (dynamic shared memory)
   __shared__ unsigned long long s_item;
+  __shared__ unsigned long long s_next;
   uint32_t* tab = reinterpret_cast<uint32_t*>(tab4);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long acc = 0, probes = 0;
@@ -276,9 +289,9 @@ k_hash_intersect(EdgeSrc s, const uint2* __restrict__ items, uint64_t nitems,
     const uint32_t o = item.x, slot = item.y >> 16, nsl = item.y & 0xFFFFu;
     const uint64_t T0 = ostart[o], T = owner_cnt[o];
     const uint64_t ta = T0 + T * slot / nsl, tb = T0 + T * (slot + 1) / nsl;
-    const int64_t ro = s.off[o];
-    const uint32_t d = (uint32_t)(s.off[o + 1] - ro);
-    const uint32_t nwin = (uint32_t)((d + kWindow - 1) / kWindow);
+    const int64_t ro = off[o];
+    const uint32_t d = (uint32_t)(off[o + 1] - ro);
+    const uint32_t nwin = (d + kWindow - 1) / kWindow;
     uint32_t nb = kHashBuckets;
     if (nwin == 1) {
       nb = 32;
@@ -287,48 +300,49 @@ k_hash_intersect(EdgeSrc s, const uint2* __restrict__ items, uint64_t nitems,
     const uint32_t mask = nb - 1;
     const uint32_t shift = 32u - (uint32_t)(__ffs(nb) - 1);
     for (uint32_t wdx = 0; wdx < nwin; ++wdx) {
-      const uint32_t wb = wdx * (uint32_t)kWindow;
-      const uint32_t we = min(d, wb + (uint32_t)kWindow);
-      const uint32_t lo = s.cols[ro + wb], hi = s.cols[ro + we - 1];
+      const uint32_t wb = wdx * kWindow;
+      const uint32_t we = min(d, wb + kWindow);
+      const uint32_t hi = (wdx + 1 == nwin) ? kEmpty - 1u : cols[ro + we - 1];
       for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x)
         tab4[k] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+      if (threadIdx.x == 0) s_next = ta;
       __syncthreads();
       for (uint32_t k = wb + threadIdx.x; k < we; k += blockDim.x)
-        table_insert(tab, shift, mask, s.cols[ro + k]);
+        table_insert(tab, shift, mask, cols[ro + k]);
       __syncthreads();
-      for (uint64_t t = ta + wid; t < tb; t += kHashWarps) {
-        const uint32_t idx = tasks[t];
-        uint32_t u, v;
-        edge_at<M>(s, idx, u, v);
-        const uint32_t p = (o == u) ? v : u;
-        Runs r;
-        probe_runs<M>(s, idx, u, v, p, r);
+      while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&s_next, 1ull);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if (t >= tb) break;
+        const uint4 ds = descs[t];
+        const uint32_t* P = pcols + ds.x;
         unsigned c = 0;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (q >= r.n) break;
-          const uint32_t* run = r.ptr[q];
-          uint32_t a = 0, bnd = r.len[q];
-          if (nwin > 1) {  // cut the run to the window's id range
-            uint32_t x = 0;
-            if (lane == 0) x = lb32(run, bnd, lo);
-            else if (lane == 1) x = lb32(run, bnd, hi + 1u);
-            a = __shfl_sync(0xFFFFFFFFu, x, 0);
-            bnd = __shfl_sync(0xFFFFFFFFu, x, 1);
+        if (nwin == 1) {
+          for (uint32_t k = lane; k < ds.y; k += 32) c += table_find(tab4, shift, mask, __ldg(P + k));
+          for (uint32_t k = ds.z + lane; k < ds.w; k += 32)
+            c += table_find(tab4, shift, mask, __ldg(P + k));
+          if (lane == 0) probes += desc_work(ds);
+        } else {
+          uint2 cur = wdx == 0 ? make_uint2(0u, ds.z) : cursors[t];
+          const uint32_t p0 = cur.x, p1 = cur.y;
+          c = probe_run_window(P, cur.x, ds.y, hi, tab4, shift, mask);
+          c += probe_run_window(P, cur.y, ds.w, hi, tab4, shift, mask);
+          if (lane == 0) {
+            probes += (cur.x - p0) + (cur.y - p1);
+            if (wdx + 1 < nwin) cursors[t] = cur;
           }
-          for (uint32_t k = a + lane; k < bnd; k += 32) c += table_find(tab4, shift, mask, run[k]);
-          if (lane == 0) probes += bnd - a;
         }
         acc += c;
         if (per_edge) {
           const unsigned long long tsum = warp_sum_u64(c);
-          if (lane == 0 && tsum) atomicAdd(&per_edge[idx], (uint32_t)tsum);
+          if (lane == 0 && tsum) atomicAdd(&per_edge[task_idx[t]], (uint32_t)tsum);
         }
       }
       __syncthreads();
     }
   }
-  // block reduction of the count and the probe total
+  // block reduction of the count and the lookup total
   __shared__ unsigned long long red[2][kHashWarps];
   acc = warp_sum_u64(acc);
   probes = warp_sum_u64(probes);
@@ -352,28 +366,15 @@ k_hash_intersect(EdgeSrc s, const uint2* __restrict__ items, uint64_t nitems,
 int merge_small_edges(tc_graph* g, int mode, const uint32_t* list, uint64_t nlist,
                       const int64_t* ustart, uint32_t* per_edge);
 
-int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge) {
+template <int M>
+static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const uint32_t* pcols,
+                           const int64_t* ustart, uint32_t* per_edge) {
   cudaStream_t st = g->stream;
   const int T = 256;
-  EdgeSrc s{};
-  s.off = g->off;
-  s.cols = g->cols;
-  uint64_t nidx;
-  if (mode == kModeCover) {
-    s.H = g->cover.p;
-    s.hoff = g->hoff.p;
-    s.seg = g->seg.p;
-    s.scols = g->scols.p;
-    nidx = (uint64_t)g->num_cover;
-  } else {
-    s.erow = g->erow.p;
-    s.ustart = ustart;
-    nidx = (uint64_t)g->nnz;
-  }
-  if (nidx == 0) return TC_OK;
-  DevBuf<uint32_t> owner_cnt, cursor, small_list, tasks;
+  DevBuf<uint32_t> owner_cnt, cursor, small_list, task_idx;
   DevBuf<unsigned long long> owner_work, ostart, nslots;
-  DevBuf<uint2> items;
+  DevBuf<uint4> descs;
+  DevBuf<uint2> items, cursors;
   TC_TRY(owner_cnt.alloc(g->n, st));
   TC_TRY(cursor.alloc(g->n, st));
   TC_TRY(owner_work.alloc(g->n, st));
@@ -384,12 +385,8 @@ int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge)
   TC_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(uint32_t) * g->n, st));
   TC_CUDA(cudaMemsetAsync(owner_work.p, 0, sizeof(unsigned long long) * g->n, st));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlQ0, 0, sizeof(unsigned long long), st));
-  if (mode == kModeCover)
-    launch(k_bucket_count<kModeCover>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx,
-           owner_cnt.p, owner_work.p, small_list.p, g->ctrl.p);
-  else
-    launch(k_bucket_count<kModePlain>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx,
-           owner_cnt.p, owner_work.p, small_list.p, g->ctrl.p);
+  launch(k_bucket_count<M>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx, owner_cnt.p,
+         owner_work.p, small_list.p, g->ctrl.p);
   launch(k_u32_to_u64, grid_for(g->n, T), T, 0, st, owner_cnt.p, g->n, ostart.p);
   TC_TRY(exclusive_scan_u64(ostart.p, g->n, g->ctrl.p + kCtrlTmp, st));
   launch(k_item_counts, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
@@ -402,15 +399,13 @@ int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge)
   const uint64_t nsmall = g->ctrl_host[kCtrlQ0];
   const uint64_t ntasks = g->ctrl_host[kCtrlTmp];
   const uint64_t nitems = g->ctrl_host[kCtrlQ1];
-  TC_TRY(tasks.alloc(ntasks, st));
+  TC_TRY(descs.alloc(ntasks, st));
+  TC_TRY(cursors.alloc(ntasks, st));
+  if (per_edge) TC_TRY(task_idx.alloc(ntasks, st));
   TC_TRY(items.alloc(nitems, st));
   if (ntasks > 0) {
-    if (mode == kModeCover)
-      launch(k_bucket_scatter<kModeCover>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p,
-             cursor.p, tasks.p);
-    else
-      launch(k_bucket_scatter<kModePlain>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p,
-             cursor.p, tasks.p);
+    launch(k_bucket_scatter<M>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p, cursor.p,
+           descs.p, per_edge ? task_idx.p : (uint32_t*)nullptr);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
            nslots.p, items.p);
   }
@@ -420,23 +415,35 @@ int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge)
   if (nitems > 0) {
     const int grid = sm_count() * 3;
     const size_t smem = sizeof(uint4) * kHashBuckets;
-    if (mode == kModeCover) {
-      TC_CUDA(cudaFuncSetAttribute(k_hash_intersect<kModeCover>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      launch(k_hash_intersect<kModeCover>, grid, kHashThreads, smem, st, s, items.p, nitems,
-             ostart.p, owner_cnt.p, tasks.p, per_edge, g->ctrl.p + kCtrlWork, g->ctrl.p);
-    } else {
-      TC_CUDA(cudaFuncSetAttribute(k_hash_intersect<kModePlain>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      launch(k_hash_intersect<kModePlain>, grid, kHashThreads, smem, st, s, items.p, nitems,
-             ostart.p, owner_cnt.p, tasks.p, per_edge, g->ctrl.p + kCtrlWork, g->ctrl.p);
-    }
+    TC_CUDA(cudaFuncSetAttribute(k_hash_intersect<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    launch(k_hash_intersect<M>, grid, kHashThreads, smem, st, g->off, g->cols, pcols, items.p,
+           nitems, ostart.p, owner_cnt.p, descs.p, task_idx.p, cursors.p, per_edge,
+           g->ctrl.p + kCtrlWork, g->ctrl.p);
     TC_CUDA(cudaGetLastError());
   }
   cudaEventRecord(g->ev[7], st);  // end of the hash kernel
-  if (nsmall > 0)
-    TC_TRY(merge_small_edges(g, mode, small_list.p, nsmall, ustart, per_edge));
+  if (nsmall > 0) TC_TRY(merge_small_edges(g, M, small_list.p, nsmall, ustart, per_edge));
   return TC_OK;
+}
+
+// Requires |edges| < 2^32 and nnz < 2^32 (32-bit task indices and row
+// positions); callers fall back to the merge kernels otherwise.
+int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge) {
+  EdgeSrc s{};
+  s.off = g->off;
+  s.cols = g->cols;
+  if (mode == kModeCover) {
+    s.H = g->cover.p;
+    s.hoff = g->hoff.p;
+    s.seg = g->seg.p;
+    if (g->num_cover == 0) return TC_OK;
+    return hash_count_mode<kModeCover>(g, s, (uint64_t)g->num_cover, g->scols.p, ustart, per_edge);
+  }
+  s.erow = g->erow.p;
+  s.ustart = ustart;
+  if (g->nnz == 0) return TC_OK;
+  return hash_count_mode<kModePlain>(g, s, (uint64_t)g->nnz, g->cols, ustart, per_edge);
 }
 
 }  // namespace tc

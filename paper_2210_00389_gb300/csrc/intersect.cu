@@ -286,7 +286,7 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
   if (per_edge_out && g->num_cover > 0)
     TC_CUDA(cudaMemsetAsync(per_edge_out, 0, sizeof(uint32_t) * (size_t)g->num_cover, s));
-  const bool hashed = g->num_cover < (int64_t)0xFFFFFFFFll;
+  const bool hashed = g->num_cover < (int64_t)0xFFFFFFFFll && g->nnz < (int64_t)0xFFFFFFFFll;
   cudaEventRecord(g->ev[4], s);
   if (hashed) {
     TC_TRY(hash_count(g, 0, nullptr, per_edge_out));

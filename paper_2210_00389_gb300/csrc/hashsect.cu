@@ -20,7 +20,9 @@
 // row array, R1 = [base, base + x) and R2 = [base + cut, base + end)
 // (cover: R1 = level l-1, R2 = same level above v followed by level l+1,
 // which are adjacent in the segmented row), stored as a 16-byte descriptor
-// per edge by the bucketing step.
+// per edge by the bucketing step.  R1 is sorted; for cover, R2 is two
+// sorted pieces split at base + z (z kept in a side array, used only by
+// windowed owners, which need sorted runs).
 //
 // Bucketing (a3) is a counting sort of the edges by owner.  Owners of degree
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
@@ -104,6 +106,13 @@ __device__ __forceinline__ uint4 probe_desc(const EdgeSrc& s, uint64_t idx, uint
 
 __device__ __forceinline__ uint32_t desc_work(uint4 d) { return d.y + (d.w - d.z); }
 
+// Split point of R2 (relative to base): start of level l+1 for cover.
+template <int M>
+__device__ __forceinline__ uint32_t probe_split(const EdgeSrc& s, uint32_t p, uint4 d) {
+  if (M == kModeCover) return s.seg[p].z;
+  return d.w;
+}
+
 // ------------------------------------------------------------------ bucketing
 
 // Per edge: owners of degree <= kSmallOwner go to the small list, others
@@ -148,7 +157,7 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
 template <int M>
 __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long long* __restrict__ ostart,
                                  uint32_t* __restrict__ cursor, uint4* __restrict__ descs,
-                                 uint32_t* __restrict__ task_idx) {
+                                 uint32_t* __restrict__ task_split, uint32_t* __restrict__ task_idx) {
   uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (; idx < nidx; idx += stride) {
@@ -158,7 +167,9 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
     owner_probe(s.off, u, v, o, p, dout);
     if (dout <= kSmallOwner) continue;
     const unsigned long long t = ostart[o] + atomicAdd(&cursor[o], 1u);
-    descs[t] = probe_desc<M>(s, idx, u, v, p);
+    const uint4 d = probe_desc<M>(s, idx, u, v, p);
+    descs[t] = d;
+    task_split[t] = probe_split<M>(s, p, d);
     if (task_idx) task_idx[t] = (uint32_t)idx;
   }
 }
@@ -270,7 +281,8 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  const uint32_t* __restrict__ pcols, const uint2* __restrict__ items,
                  uint64_t nitems, const unsigned long long* __restrict__ ostart,
                  const uint32_t* __restrict__ owner_cnt, const uint4* __restrict__ descs,
-                 const uint32_t* __restrict__ task_idx, uint2* __restrict__ cursors,
+                 const uint32_t* __restrict__ task_split, const uint32_t* __restrict__ task_idx,
+                 uint4* __restrict__ cursors,
                  uint32_t* __restrict__ per_edge, unsigned long long* item_counter,
                  unsigned long long* ctrl) {
   extern __shared__ uint4 tab4[];  // kHashBuckets buckets (dynamic shared memory)
@@ -324,12 +336,15 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
             c += table_find(tab4, shift, mask, __ldg(P + k));
           if (lane == 0) probes += desc_work(ds);
         } else {
-          uint2 cur = wdx == 0 ? make_uint2(0u, ds.z) : cursors[t];
-          const uint32_t p0 = cur.x, p1 = cur.y;
+          // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
+          const uint32_t z = task_split[t];
+          uint4 cur = wdx == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
+          const uint32_t p0 = cur.x, p1 = cur.y, p2 = cur.z;
           c = probe_run_window(P, cur.x, ds.y, hi, tab4, shift, mask);
-          c += probe_run_window(P, cur.y, ds.w, hi, tab4, shift, mask);
+          c += probe_run_window(P, cur.y, z, hi, tab4, shift, mask);
+          c += probe_run_window(P, cur.z, ds.w, hi, tab4, shift, mask);
           if (lane == 0) {
-            probes += (cur.x - p0) + (cur.y - p1);
+            probes += (cur.x - p0) + (cur.y - p1) + (cur.z - p2);
             if (wdx + 1 < nwin) cursors[t] = cur;
           }
         }
@@ -371,10 +386,11 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
                            const int64_t* ustart, uint32_t* per_edge) {
   cudaStream_t st = g->stream;
   const int T = 256;
-  DevBuf<uint32_t> owner_cnt, cursor, small_list, task_idx;
+  DevBuf<uint32_t> owner_cnt, cursor, small_list, task_idx, task_split;
   DevBuf<unsigned long long> owner_work, ostart, nslots;
   DevBuf<uint4> descs;
-  DevBuf<uint2> items, cursors;
+  DevBuf<uint2> items;
+  DevBuf<uint4> cursors;
   TC_TRY(owner_cnt.alloc(g->n, st));
   TC_TRY(cursor.alloc(g->n, st));
   TC_TRY(owner_work.alloc(g->n, st));
@@ -401,11 +417,12 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   const uint64_t nitems = g->ctrl_host[kCtrlQ1];
   TC_TRY(descs.alloc(ntasks, st));
   TC_TRY(cursors.alloc(ntasks, st));
+  TC_TRY(task_split.alloc(ntasks, st));
   if (per_edge) TC_TRY(task_idx.alloc(ntasks, st));
   TC_TRY(items.alloc(nitems, st));
   if (ntasks > 0) {
     launch(k_bucket_scatter<M>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p, cursor.p,
-           descs.p, per_edge ? task_idx.p : (uint32_t*)nullptr);
+           descs.p, task_split.p, per_edge ? task_idx.p : (uint32_t*)nullptr);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
            nslots.p, items.p);
   }
@@ -418,7 +435,7 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
     TC_CUDA(cudaFuncSetAttribute(k_hash_intersect<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     launch(k_hash_intersect<M>, grid, kHashThreads, smem, st, g->off, g->cols, pcols, items.p,
-           nitems, ostart.p, owner_cnt.p, descs.p, task_idx.p, cursors.p, per_edge,
+           nitems, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p, cursors.p, per_edge,
            g->ctrl.p + kCtrlWork, g->ctrl.p);
     TC_CUDA(cudaGetLastError());
   }

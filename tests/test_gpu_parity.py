@@ -170,6 +170,27 @@ def test_invalid_graphs_are_rejected(tc, name, off, cols, flags):
     assert e.value.status == tc.TC_ERR_INVALID_GRAPH
 
 
+@pytest.mark.slow
+def test_rmat_s18_hub_windows(tc):
+    """R-MAT scale 18 (max degree ~25K, above one shared-memory table):
+    every per-edge count, levels and H against the oracle, and the plain
+    total, so hub rows processed in several windows are covered in full."""
+    g = gg.rmat(18, 16, seed=2, relabel_seed=2 + 2**32)
+    assert g.degrees().max() > 3 * 8192
+    L, _ = oracle.bfs_levels(g)
+    H = oracle.cover_edges(g, L)
+    want = oracle.cetc_edge_counts(g, L, H)
+    with tc.Graph(g.offsets, g.cols) as G:
+        assert np.array_equal(G.levels()[0], L)
+        assert np.array_equal(G.cover_edges(), H)
+        got = G.cover_edge_counts()
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, f"{bad.size} edges differ, first {H[bad[:5]].tolist()}"
+        T = int(want.astype(np.int64).sum())
+        assert G.count(tc.TC_MODE_COVER) == T
+        assert G.count(tc.TC_MODE_PLAIN) == T
+
+
 def test_degenerate(tc):
     for g in (gg.empty(0), gg.empty(1), gg.empty(5000), gg.path(2), gg.complete(3)):
         check_graph(tc, g)

@@ -178,6 +178,30 @@ typedef struct {
 } tc_stats_t;
 TC_API int tc_graph_stats(const tc_graph* g, tc_stats_t* out);
 
+/* Plain all-edge triangle count (as tc_count with TC_MODE_PLAIN) of a
+ * device-resident CSR, without allocating any device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc/cudaFree at this point -- those calls can synchronize the
+ * device, which a latency-bound loop overlapping several streams must avoid;
+ * applications whose device memory is owned by another allocator or budgeted
+ * once at start-up may not allocate behind it.
+ *   offsets, cols: device memory, a valid symmetric CSR (the rules above;
+ *     not validated here; column ids >= n are skipped).
+ *   count_out: device memory, receives the count (uint64).
+ *   cuda_stream: stream for the work (NULL = legacy default stream).
+ * Asynchronous: returns after enqueueing; read *count_out after the stream
+ * completes.  Scratch is one static device array of 16 MiB + 256 B that
+ * every GPU loading the library keeps until the process exits; n may be at
+ * most 4,194,304 (TC_ERR_CAPACITY beyond it, checked before any work).  The
+ * first call on a device looks up that device's scratch address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and give wrong counts, so serialize them (one stream, or events).
+ * Errors: TC_ERR_CAPACITY, TC_ERR_INVALID_ARG (NULL, nnz < 0, or a pointer
+ * that is not device memory), TC_ERR_CUDA. */
+TC_API int tc_count_plain_static(const int64_t* offsets, const uint32_t* cols, uint32_t n,
+                                 int64_t nnz, uint64_t* count_out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- batch */
 /* Tunables of the intersection (NULL anywhere = built-in / autotuned). */
 typedef struct {

@@ -104,6 +104,7 @@ _SIGS = {
     "tc_cover_edges": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _i64p]),
     "tc_count": (ctypes.c_int, [_vp, ctypes.c_int, _u64p]),
     "tc_cover_edge_counts": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
+    "tc_count_plain_static": (ctypes.c_int, [_vp, _vp, ctypes.c_uint32, ctypes.c_int64, _vp, _vp]),
     "tc_count_batch": (ctypes.c_int, [ctypes.POINTER(CSRView), ctypes.c_int32, ctypes.c_int,
                                       ctypes.POINTER(Options), _vp, _u64p, _ip]),
     "tc_serve_create": (ctypes.c_int, [ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]),
@@ -283,6 +284,19 @@ def tc_cover_edge_counts(g: int, out=None):
     cap = out.numel() if _is_torch(out) else out.size
     _check(_lib.tc_cover_edge_counts(g, op, cap), "tc_cover_edge_counts")
     return out[:cnt.value]
+
+
+def tc_count_plain_static(offsets, cols, count_out, n: int | None = None, stream=None) -> None:
+    """Plain all-edge count of a device CSR into the device tensor
+    ``count_out`` (int64/uint64, one element) without any device
+    allocation; asynchronous on ``stream``."""
+    op, od = _ptr(offsets)
+    cp, cd = _ptr(cols)
+    outp, outd = _ptr(count_out)
+    if n is None:
+        n = offsets.shape[0] - 1
+    _check(_lib.tc_count_plain_static(op, cp, n, cols.shape[0], outp, _stream_handle(stream)),
+           "tc_count_plain_static")
 
 
 def tc_count_batch(graphs, mode: int = TC_MODE_COVER, opt: Options | None = None, stream=None):

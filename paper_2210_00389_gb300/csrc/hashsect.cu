@@ -29,19 +29,20 @@
 // split into work items (owner, slot) of about kItemWork lookups; a CTA
 // takes an item, builds a bucketized hash table of N(o) in shared memory
 // (4 slots of 4 bytes per bucket, load <= 1/2, one 16-byte shared load per
-// lookup) and its warps take the item's edges from a shared counter.  Rows
-// longer than kWindow are processed in windows of kWindow consecutive
-// entries (an id range); every probe run keeps a cursor across windows, so
-// each probe element is looked up once.
+// lookup) and its warps take the item's edges from a shared counter.
+// Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (six
+// per SM); larger owners use 1024-thread CTAs with 192 KB tables.  Rows
+// longer than a table (24,576 entries) are processed in windows of
+// consecutive entries (an id range); every probe run keeps a cursor across
+// windows, so each probe element is looked up once.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace tc {
 
-constexpr int kHashThreads = 512;
-constexpr int kHashWarps = kHashThreads / 32;
-constexpr int kHashBuckets = 4096;                // 64 KB of uint4 buckets
-constexpr uint32_t kWindow = 2 * kHashBuckets;    // owner entries per table
 constexpr uint32_t kSmallOwner = 64;              // owners this small use the merge
+constexpr uint32_t kMediumMax = 4096;             // larger owners use the big tables
 constexpr unsigned long long kItemWork = 1ull << 19;  // target lookups per work item
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
@@ -173,7 +174,6 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
     if (task_idx) task_idx[t] = (uint32_t)idx;
   }
 }
-
 // Slots per owner: about kItemWork lookups per item, and at least 4 lookups
 // per table entry built (each item builds N(o)'s table).
 __device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long work, uint32_t d) {
@@ -188,27 +188,44 @@ __device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long
   return (uint32_t)s;
 }
 
+// Owners of degree <= kMediumMax go to the 256-thread kernel with small
+// tables, larger ones to the 1024-thread kernel with large tables.
+__device__ __forceinline__ int owner_class(uint32_t d) { return d > kMediumMax ? 1 : 0; }
+
+// Per owner: its slot count; totals per class in ctrl[kCtrlItems + class].
 __global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
                               const uint32_t* __restrict__ owner_cnt,
                               const unsigned long long* __restrict__ owner_work,
-                              unsigned long long* __restrict__ nslots) {
+                              unsigned long long* ctrl) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (; o < (int64_t)n; o += stride)
-    nslots[o] = owner_slots(owner_cnt[o], owner_work[o], degree(off, (uint32_t)o));
+  unsigned long long t[2] = {0ull, 0ull};
+  for (; o < (int64_t)n; o += stride) {
+    const uint32_t d = degree(off, (uint32_t)o);
+    t[owner_class(d)] += owner_slots(owner_cnt[o], owner_work[o], d);
+  }
+  for (int c = 0; c < 2; ++c) {
+    unsigned long long x = t[c];
+    for (int k = 16; k > 0; k >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, k);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&ctrl[kCtrlItems + c], x);
+  }
 }
 
-// items[k] = (owner, slot << 16 | slots)
+// items of class c at items_c[atomic cursor]: (owner, slot << 16 | slots)
 __global__ void k_item_write(const int64_t* __restrict__ off, uint32_t n,
                              const uint32_t* __restrict__ owner_cnt,
                              const unsigned long long* __restrict__ owner_work,
-                             const unsigned long long* __restrict__ item_start,
-                             uint2* __restrict__ items) {
+                             uint2* __restrict__ items0, uint2* __restrict__ items1,
+                             unsigned long long* cursors) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; o < (int64_t)n; o += stride) {
-    const uint32_t s = owner_slots(owner_cnt[o], owner_work[o], degree(off, (uint32_t)o));
-    const unsigned long long b = item_start[o];
+    const uint32_t d = degree(off, (uint32_t)o);
+    const uint32_t s = owner_slots(owner_cnt[o], owner_work[o], d);
+    if (s == 0) continue;
+    const int c = owner_class(d);
+    const unsigned long long b = atomicAdd(&cursors[c], (unsigned long long)s);
+    uint2* items = c ? items1 : items0;
     for (uint32_t k = 0; k < s; ++k) items[b + k] = make_uint2((uint32_t)o, (k << 16) | s);
   }
 }
@@ -221,32 +238,36 @@ __global__ void k_u32_to_u64(const uint32_t* __restrict__ a, uint32_t n, unsigne
 
 // ------------------------------------------------------------------ hashing
 
-// Fibonacci hashing: the top log2(buckets) bits of w * 2^32/phi.
-__device__ __forceinline__ uint32_t hash_bucket(uint32_t w, uint32_t shift) {
-  return (w * 0x9E3779B1u) >> shift;
+// Bucket of w among nb buckets: multiply-high of a Fibonacci hash (Knuth's
+// multiplicative hashing with 2^32/phi; Lemire's multiply-shift range map),
+// so nb need not be a power of two.
+__device__ __forceinline__ uint32_t hash_bucket(uint32_t w, uint32_t nb) {
+  return __umulhi(w * 0x9E3779B1u, nb);
 }
 
-__device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t shift, uint32_t mask,
-                                             uint32_t w) {
-  uint32_t b = hash_bucket(w, shift);
+__device__ __forceinline__ uint32_t next_bucket(uint32_t b, uint32_t nb) {
+  return b + 1 == nb ? 0u : b + 1;
+}
+
+__device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t nb, uint32_t w) {
+  uint32_t b = hash_bucket(w, nb);
   while (true) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (atomicCAS(&tab[4 * b + k], kEmpty, w) == kEmpty) return;
-    b = (b + 1) & mask;
+    b = next_bucket(b, nb);
   }
 }
 
 // Slots of a bucket fill in order and never empty again, so a bucket whose
 // last slot is empty ends the search.
-__device__ __forceinline__ unsigned table_find(const uint4* tab4, uint32_t shift, uint32_t mask,
-                                               uint32_t w) {
-  uint32_t b = hash_bucket(w, shift);
+__device__ __forceinline__ unsigned table_find(const uint4* tab4, uint32_t nb, uint32_t w) {
+  uint32_t b = hash_bucket(w, nb);
   while (true) {
     const uint4 q = tab4[b];
     if (q.x == w || q.y == w || q.z == w || q.w == w) return 1u;
     if (q.w == kEmpty) return 0u;
-    b = (b + 1) & mask;
+    b = next_bucket(b, nb);
   }
 }
 
@@ -255,37 +276,70 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
   return x;
 }
 
-// Look up P[pos..end) while the elements are <= hi; returns the lane's hits
-// and advances pos past the elements looked up.
-__device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict__ P, uint32_t& pos,
-                                                     uint32_t end, uint32_t hi, const uint4* tab4,
-                                                     uint32_t shift, uint32_t mask) {
+constexpr int kUnroll = 4;  // probe loads in flight per lane
+
+// All probe elements of a descriptor (runs [0, x) and [cut, end) of P,
+// taken as one index space of x + end - cut elements), kUnroll loads per
+// lane issued before their lookups.
+__device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
+                                              const uint4* tab4, uint32_t nb) {
   const int lane = threadIdx.x & 31;
+  const uint32_t x = ds.y, shift2 = ds.z - ds.y;  // element k >= x sits at P[k + cut - x]
+  const uint32_t total = ds.y + (ds.w - ds.z);
   unsigned c = 0;
-  while (pos < end) {
-    const uint32_t k = pos + lane;
-    const bool valid = k < end;
-    const uint32_t w = valid ? __ldg(P + k) : kEmpty;
-    const bool in = valid && w <= hi;
-    if (in) c += table_find(tab4, shift, mask, w);
-    const uint32_t nin = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in));
-    pos += nin;  // the elements <= hi form a prefix (runs are sorted)
-    if (nin < 32) break;
+  for (uint32_t k0 = 0; k0 < total; k0 += 32 * kUnroll) {
+    uint32_t w[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) {
+      const uint32_t k = k0 + j * 32 + lane;
+      w[j] = k < total ? __ldg(P + (k < x ? k : k + shift2)) : kEmpty;
+    }
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j)
+      if (w[j] != kEmpty) c += table_find(tab4, nb, w[j]);
   }
   return c;
 }
 
-template <int M>
-__global__ void __launch_bounds__(kHashThreads, 3)
+// Look up P[pos..end) while the elements are <= hi (a sorted run); returns
+// the lane's hits and advances pos past the elements looked up.
+__device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict__ P, uint32_t& pos,
+                                                     uint32_t end, uint32_t hi, const uint4* tab4,
+                                                     uint32_t nb) {
+  const int lane = threadIdx.x & 31;
+  unsigned c = 0;
+  while (pos < end) {
+    uint32_t w[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) {
+      const uint32_t k = pos + j * 32 + lane;
+      w[j] = k < end ? __ldg(P + k) : kEmpty;
+    }
+    uint32_t nin = 0;
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) {
+      const bool in = w[j] <= hi;  // kEmpty > hi: padding never counts
+      if (in) c += table_find(tab4, nb, w[j]);
+      nin += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in));
+    }
+    pos += nin;  // the elements <= hi form a prefix of the sorted run
+    if (nin < 32 * kUnroll) break;
+  }
+  return c;
+}
+
+template <int M, int THREADS, int BUCKETS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
 k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                  const uint32_t* __restrict__ pcols, const uint2* __restrict__ items,
                  uint64_t nitems, const unsigned long long* __restrict__ ostart,
                  const uint32_t* __restrict__ owner_cnt, const uint4* __restrict__ descs,
                  const uint32_t* __restrict__ task_split, const uint32_t* __restrict__ task_idx,
-                 uint4* __restrict__ cursors,
-                 uint32_t* __restrict__ per_edge, unsigned long long* item_counter,
-                 unsigned long long* ctrl) {
-  extern __shared__ uint4 tab4[];  // kHashBuckets buckets (dynamic shared memory)
+                 uint4* __restrict__ cursors, uint32_t* __restrict__ per_edge,
+                 unsigned long long* item_counter, unsigned long long* ctrl) {
+  constexpr int kWarps = THREADS / 32;
+  constexpr uint32_t kWin = 2 * BUCKETS;  // owner entries per table (load <= 1/2)
+  extern __shared__ uint4 tab4[];         // BUCKETS buckets (dynamic shared memory)
   __shared__ unsigned long long s_item;
   __shared__ unsigned long long s_next;
   uint32_t* tab = reinterpret_cast<uint32_t*>(tab4);
@@ -303,24 +357,17 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
     const uint64_t ta = T0 + T * slot / nsl, tb = T0 + T * (slot + 1) / nsl;
     const int64_t ro = off[o];
     const uint32_t d = (uint32_t)(off[o + 1] - ro);
-    const uint32_t nwin = (d + kWindow - 1) / kWindow;
-    uint32_t nb = kHashBuckets;
-    if (nwin == 1) {
-      nb = 32;
-      while (nb * 2 < d) nb <<= 1;  // >= 2 slots per entry
-    }
-    const uint32_t mask = nb - 1;
-    const uint32_t shift = 32u - (uint32_t)(__ffs(nb) - 1);
+    const uint32_t nwin = (d + kWin - 1) / kWin;
+    const uint32_t nb = nwin == 1 ? max(32u, (d + 1) / 2) : (uint32_t)BUCKETS;  // >= 2 slots/entry
     for (uint32_t wdx = 0; wdx < nwin; ++wdx) {
-      const uint32_t wb = wdx * kWindow;
-      const uint32_t we = min(d, wb + kWindow);
+      const uint32_t wb = wdx * kWin;
+      const uint32_t we = min(d, wb + kWin);
       const uint32_t hi = (wdx + 1 == nwin) ? kEmpty - 1u : cols[ro + we - 1];
-      for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x)
+      for (uint32_t k = threadIdx.x; k < nb; k += THREADS)
         tab4[k] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
       if (threadIdx.x == 0) s_next = ta;
       __syncthreads();
-      for (uint32_t k = wb + threadIdx.x; k < we; k += blockDim.x)
-        table_insert(tab, shift, mask, cols[ro + k]);
+      for (uint32_t k = wb + threadIdx.x; k < we; k += THREADS) table_insert(tab, nb, cols[ro + k]);
       __syncthreads();
       while (true) {
         unsigned long long t = 0;
@@ -329,20 +376,18 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         if (t >= tb) break;
         const uint4 ds = descs[t];
         const uint32_t* P = pcols + ds.x;
-        unsigned c = 0;
+        unsigned c;
         if (nwin == 1) {
-          for (uint32_t k = lane; k < ds.y; k += 32) c += table_find(tab4, shift, mask, __ldg(P + k));
-          for (uint32_t k = ds.z + lane; k < ds.w; k += 32)
-            c += table_find(tab4, shift, mask, __ldg(P + k));
+          c = probe_all(P, ds, tab4, nb);
           if (lane == 0) probes += desc_work(ds);
         } else {
           // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
           const uint32_t z = task_split[t];
           uint4 cur = wdx == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
           const uint32_t p0 = cur.x, p1 = cur.y, p2 = cur.z;
-          c = probe_run_window(P, cur.x, ds.y, hi, tab4, shift, mask);
-          c += probe_run_window(P, cur.y, z, hi, tab4, shift, mask);
-          c += probe_run_window(P, cur.z, ds.w, hi, tab4, shift, mask);
+          c = probe_run_window(P, cur.x, ds.y, hi, tab4, nb);
+          c += probe_run_window(P, cur.y, z, hi, tab4, nb);
+          c += probe_run_window(P, cur.z, ds.w, hi, tab4, nb);
           if (lane == 0) {
             probes += (cur.x - p0) + (cur.y - p1) + (cur.z - p2);
             if (wdx + 1 < nwin) cursors[t] = cur;
@@ -358,14 +403,14 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
     }
   }
   // block reduction of the count and the lookup total
-  __shared__ unsigned long long red[2][kHashWarps];
+  __shared__ unsigned long long red[2][kWarps];
   acc = warp_sum_u64(acc);
   probes = warp_sum_u64(probes);
   if (lane == 0) { red[0][wid] = acc; red[1][wid] = probes; }
   __syncthreads();
   if (wid == 0) {
-    unsigned long long a = lane < kHashWarps ? red[0][lane] : 0ull;
-    unsigned long long b = lane < kHashWarps ? red[1][lane] : 0ull;
+    unsigned long long a = lane < kWarps ? red[0][lane] : 0ull;
+    unsigned long long b = lane < kWarps ? red[1][lane] : 0ull;
     a = warp_sum_u64(a);
     b = warp_sum_u64(b);
     if (lane == 0) {
@@ -373,6 +418,31 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
       if (b) atomicAdd(&ctrl[kCtrlElems], b);
     }
   }
+}
+
+// Table configurations: medium owners (degree <= kMediumMax) in 256-thread
+// CTAs with 32 KB tables, six per SM; large owners in 1024-thread CTAs with
+// 192 KB tables (windows of 24,576 entries), one per SM.
+constexpr int kMedThreads = 256, kMedBuckets = 2048, kMedPerSM = 6;
+constexpr int kBigThreads = 1024, kBigBuckets = 12288, kBigPerSM = 1;
+static_assert(2 * kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
+
+template <int M, int THREADS, int BUCKETS, int MINB>
+static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, uint64_t nitems,
+                       const unsigned long long* ostart, const uint32_t* owner_cnt,
+                       const uint4* descs, const uint32_t* task_split, const uint32_t* task_idx,
+                       uint4* cursors, uint32_t* per_edge, unsigned long long* counter) {
+  if (nitems == 0) return TC_OK;
+  cudaStream_t st = g->stream;
+  const size_t smem = sizeof(uint4) * BUCKETS;
+  auto k = k_hash_intersect<M, THREADS, BUCKETS, MINB>;
+  TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TC_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+  const uint64_t grid = std::min<uint64_t>((uint64_t)sm_count() * MINB, nitems);
+  launch(k, (unsigned)grid, THREADS, smem, st, g->off, g->cols, pcols, items, nitems, ostart,
+         owner_cnt, descs, task_split, task_idx, cursors, per_edge, counter, g->ctrl.p);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
 }
 
 // ------------------------------------------------------------------ driver
@@ -387,59 +457,55 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   cudaStream_t st = g->stream;
   const int T = 256;
   DevBuf<uint32_t> owner_cnt, cursor, small_list, task_idx, task_split;
-  DevBuf<unsigned long long> owner_work, ostart, nslots;
-  DevBuf<uint4> descs;
-  DevBuf<uint2> items;
-  DevBuf<uint4> cursors;
+  DevBuf<unsigned long long> owner_work, ostart, counters;
+  DevBuf<uint4> descs, cursors;
+  DevBuf<uint2> items0, items1;
   TC_TRY(owner_cnt.alloc(g->n, st));
   TC_TRY(cursor.alloc(g->n, st));
   TC_TRY(owner_work.alloc(g->n, st));
   TC_TRY(ostart.alloc(g->n, st));
-  TC_TRY(nslots.alloc(g->n, st));
   TC_TRY(small_list.alloc(nidx, st));
+  TC_TRY(counters.alloc(4, st));
   TC_CUDA(cudaMemsetAsync(owner_cnt.p, 0, sizeof(uint32_t) * g->n, st));
   TC_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(uint32_t) * g->n, st));
   TC_CUDA(cudaMemsetAsync(owner_work.p, 0, sizeof(unsigned long long) * g->n, st));
+  TC_CUDA(cudaMemsetAsync(counters.p, 0, 4 * sizeof(unsigned long long), st));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlQ0, 0, sizeof(unsigned long long), st));
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlItems, 0, 2 * sizeof(unsigned long long), st));
   launch(k_bucket_count<M>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx, owner_cnt.p,
          owner_work.p, small_list.p, g->ctrl.p);
   launch(k_u32_to_u64, grid_for(g->n, T), T, 0, st, owner_cnt.p, g->n, ostart.p);
   TC_TRY(exclusive_scan_u64(ostart.p, g->n, g->ctrl.p + kCtrlTmp, st));
   launch(k_item_counts, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-         nslots.p);
-  TC_TRY(exclusive_scan_u64(nslots.p, g->n, g->ctrl.p + kCtrlQ1, st));
+         g->ctrl.p);
   TC_CUDA(cudaGetLastError());
   TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
                           cudaMemcpyDeviceToHost, st));
   TC_CUDA(cudaStreamSynchronize(st));
   const uint64_t nsmall = g->ctrl_host[kCtrlQ0];
   const uint64_t ntasks = g->ctrl_host[kCtrlTmp];
-  const uint64_t nitems = g->ctrl_host[kCtrlQ1];
+  const uint64_t nitems0 = g->ctrl_host[kCtrlItems], nitems1 = g->ctrl_host[kCtrlItems + 1];
   TC_TRY(descs.alloc(ntasks, st));
   TC_TRY(cursors.alloc(ntasks, st));
   TC_TRY(task_split.alloc(ntasks, st));
   if (per_edge) TC_TRY(task_idx.alloc(ntasks, st));
-  TC_TRY(items.alloc(nitems, st));
+  TC_TRY(items0.alloc(nitems0, st));
+  TC_TRY(items1.alloc(nitems1, st));
   if (ntasks > 0) {
     launch(k_bucket_scatter<M>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p, cursor.p,
            descs.p, task_split.p, per_edge ? task_idx.p : (uint32_t*)nullptr);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-           nslots.p, items.p);
+           items0.p, items1.p, counters.p);
   }
   TC_CUDA(cudaGetLastError());
-  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), st));
   cudaEventRecord(g->ev[6], st);  // end of bucketing
-  if (nitems > 0) {
-    const int grid = sm_count() * 3;
-    const size_t smem = sizeof(uint4) * kHashBuckets;
-    TC_CUDA(cudaFuncSetAttribute(k_hash_intersect<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    launch(k_hash_intersect<M>, grid, kHashThreads, smem, st, g->off, g->cols, pcols, items.p,
-           nitems, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p, cursors.p, per_edge,
-           g->ctrl.p + kCtrlWork, g->ctrl.p);
-    TC_CUDA(cudaGetLastError());
-  }
-  cudaEventRecord(g->ev[7], st);  // end of the hash kernel
+  TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigPerSM>(
+      g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
+      cursors.p, per_edge, counters.p + 2)));
+  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedPerSM>(
+      g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
+      cursors.p, per_edge, counters.p + 3)));
+  cudaEventRecord(g->ev[7], st);  // end of the hash kernels
   if (nsmall > 0) TC_TRY(merge_small_edges(g, M, small_list.p, nsmall, ustart, per_edge));
   return TC_OK;
 }

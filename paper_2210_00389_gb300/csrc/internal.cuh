@@ -149,6 +149,7 @@ enum CtrlSlot {
   kCtrlElems = 6,     // list elements handed to the intersection
   kCtrlTmp = 7,
   kCtrlWork = 8,      // dynamic work counter of the intersection kernels
+  kCtrlItems = 9,     // work items per table class (two slots: 9, 10)
   kCtrlSlots = 16
 };
 

@@ -301,6 +301,70 @@ __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, ui
   return c;
 }
 
+constexpr uint32_t kBatchMaxWork = 64;  // tasks with fewer lookups share a warp pass
+
+// Up to 32 tasks t0 .. t0+nt-1 at once: lane j holds task j's descriptor.
+// Tasks with fewer than kBatchMaxWork lookups are laid end to end in one
+// index space; each lane finds the task of its position by bisection over
+// the warp's inclusive prefix sums (shuffles) and looks the element up.
+// Larger tasks are then done one at a time by the whole warp.
+__device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pcols,
+                                                const uint4* __restrict__ descs, uint64_t t0,
+                                                uint32_t nt, const uint4* tab4, uint32_t nb,
+                                                unsigned long long* probes) {
+  const int lane = threadIdx.x & 31;
+  const uint4 ds = (uint32_t)lane < nt ? descs[t0 + lane] : make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t w = desc_work(ds);
+  const bool small = w < kBatchMaxWork;
+  uint32_t s = small ? w : 0u;  // inclusive prefix of the small tasks' work
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+    if (lane >= o) s += y;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, s, 31);
+  const uint32_t excl = s - (small ? w : 0u);
+  const uint32_t xr = ds.y, shift2 = ds.z - ds.y;
+  unsigned c = 0;
+  for (uint32_t k0 = 0; k0 < total; k0 += 32 * kUnroll) {
+    uint32_t e[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) {
+      const uint32_t g = k0 + j * 32 + lane;
+      // q = number of prefix values <= g = the task holding position g
+      int q = 0;
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1) {
+        const uint32_t sv = __shfl_sync(0xFFFFFFFFu, s, q + st - 1);
+        if (sv <= g) q += st;
+      }
+      const uint32_t base = __shfl_sync(0xFFFFFFFFu, ds.x, q);
+      const uint32_t xq = __shfl_sync(0xFFFFFFFFu, xr, q);
+      const uint32_t sq = __shfl_sync(0xFFFFFFFFu, shift2, q);
+      const uint32_t eq = __shfl_sync(0xFFFFFFFFu, excl, q);
+      const uint32_t loc = g - eq;
+      e[j] = g < total ? __ldg(pcols + base + (loc < xq ? loc : loc + sq)) : kEmpty;
+    }
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j)
+      if (e[j] != kEmpty) c += table_find(tab4, nb, e[j]);
+  }
+  if (lane == 0) *probes += total;
+  unsigned big = __ballot_sync(0xFFFFFFFFu, (uint32_t)lane < nt && !small);
+  while (big) {
+    const int j = __ffs(big) - 1;
+    big &= big - 1;
+    uint4 dj;
+    dj.x = __shfl_sync(0xFFFFFFFFu, ds.x, j);
+    dj.y = __shfl_sync(0xFFFFFFFFu, ds.y, j);
+    dj.z = __shfl_sync(0xFFFFFFFFu, ds.z, j);
+    dj.w = __shfl_sync(0xFFFFFFFFu, ds.w, j);
+    c += probe_all(pcols + dj.x, dj, tab4, nb);
+    if (lane == 0) *probes += desc_work(dj);
+  }
+  return c;
+}
+
 // Look up P[pos..end) while the elements are <= hi (a sorted run); returns
 // the lane's hits and advances pos past the elements looked up.
 __device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict__ P, uint32_t& pos,
@@ -328,7 +392,7 @@ __device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict_
   return c;
 }
 
-template <int M, int THREADS, int BUCKETS, int MINB>
+template <int M, int THREADS, int BUCKETS, int MINB, bool BATCH>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                  const uint32_t* __restrict__ pcols, const uint2* __restrict__ items,
@@ -369,6 +433,17 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
       __syncthreads();
       for (uint32_t k = wb + threadIdx.x; k < we; k += THREADS) table_insert(tab, nb, cols[ro + k]);
       __syncthreads();
+      if (BATCH && nwin == 1 && per_edge == nullptr) {
+        // warps take 32 edges at a time and share passes over short lists
+        while (true) {
+          unsigned long long t = 0;
+          if (lane == 0) t = atomicAdd(&s_next, 32ull);
+          t = __shfl_sync(0xFFFFFFFFu, t, 0);
+          if (t >= tb) break;
+          const uint32_t nt = (uint32_t)min((unsigned long long)32, tb - t);
+          acc += probe_batch(pcols, descs, t, nt, tab4, nb, &probes);
+        }
+      } else
       while (true) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(&s_next, 1ull);
@@ -427,7 +502,7 @@ constexpr int kMedThreads = 256, kMedBuckets = 2048, kMedPerSM = 6;
 constexpr int kBigThreads = 1024, kBigBuckets = 12288, kBigPerSM = 1;
 static_assert(2 * kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
 
-template <int M, int THREADS, int BUCKETS, int MINB>
+template <int M, int THREADS, int BUCKETS, int MINB, bool BATCH>
 static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, uint64_t nitems,
                        const unsigned long long* ostart, const uint32_t* owner_cnt,
                        const uint4* descs, const uint32_t* task_split, const uint32_t* task_idx,
@@ -435,7 +510,7 @@ static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, u
   if (nitems == 0) return TC_OK;
   cudaStream_t st = g->stream;
   const size_t smem = sizeof(uint4) * BUCKETS;
-  auto k = k_hash_intersect<M, THREADS, BUCKETS, MINB>;
+  auto k = k_hash_intersect<M, THREADS, BUCKETS, MINB, BATCH>;
   TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TC_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   const uint64_t grid = std::min<uint64_t>((uint64_t)sm_count() * MINB, nitems);
@@ -499,10 +574,10 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   }
   TC_CUDA(cudaGetLastError());
   cudaEventRecord(g->ev[6], st);  // end of bucketing
-  TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigPerSM>(
+  TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigPerSM, false>(
       g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge, counters.p + 2)));
-  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedPerSM>(
+  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedPerSM, true>(
       g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge, counters.p + 3)));
   cudaEventRecord(g->ev[7], st);  // end of the hash kernels

@@ -44,6 +44,7 @@ namespace tc {
 constexpr uint32_t kSmallOwner = 64;              // owners this small use the merge
 constexpr uint32_t kMediumMax = 4096;             // larger owners use the big tables
 constexpr unsigned long long kItemWork = 1ull << 19;  // target lookups per work item
+constexpr unsigned long long kBuildRatio = 4;     // hash an owner only if lookups >= 4 d(o)
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 enum { kModeCover = 0, kModePlain = 1 };
@@ -153,31 +154,57 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
   }
 }
 
-// Scatter every non-small edge's descriptor (and its index, for per-edge
-// counts) into its owner's task range.
+// An owner is hashed only if its edges bring at least kBuildRatio lookups
+// per table entry; the edges of other owners join the merge list.
+__device__ __forceinline__ bool owner_hashed(unsigned long long work, uint32_t d) {
+  return work >= kBuildRatio * (unsigned long long)d;
+}
+
+// Scatter every hashed edge's descriptor (and its index, for per-edge
+// counts) into its owner's task range; edges of owners too light to hash
+// are appended to the merge list.
 template <int M>
 __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long long* __restrict__ ostart,
+                                 const unsigned long long* __restrict__ owner_work,
                                  uint32_t* __restrict__ cursor, uint4* __restrict__ descs,
-                                 uint32_t* __restrict__ task_split, uint32_t* __restrict__ task_idx) {
-  uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+                                 uint32_t* __restrict__ task_split, uint32_t* __restrict__ task_idx,
+                                 uint32_t* __restrict__ small_list, unsigned long long* ctrl) {
+  const int lane = threadIdx.x & 31;
+  uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (; idx < nidx; idx += stride) {
+  for (; base < nidx; base += stride) {
+    const uint64_t idx = base + lane;
+    bool light = false;
     uint32_t u, v;
-    if (!edge_at<M>(s, idx, u, v)) continue;
-    uint32_t o, p, dout;
-    owner_probe(s.off, u, v, o, p, dout);
-    if (dout <= kSmallOwner) continue;
-    const unsigned long long t = ostart[o] + atomicAdd(&cursor[o], 1u);
-    const uint4 d = probe_desc<M>(s, idx, u, v, p);
-    descs[t] = d;
-    task_split[t] = probe_split<M>(s, p, d);
-    if (task_idx) task_idx[t] = (uint32_t)idx;
+    if (idx < nidx && edge_at<M>(s, idx, u, v)) {
+      uint32_t o, p, dout;
+      owner_probe(s.off, u, v, o, p, dout);
+      if (dout > kSmallOwner) {
+        if (owner_hashed(owner_work[o], dout)) {
+          const unsigned long long t = ostart[o] + atomicAdd(&cursor[o], 1u);
+          const uint4 d = probe_desc<M>(s, idx, u, v, p);
+          descs[t] = d;
+          task_split[t] = probe_split<M>(s, p, d);
+          if (task_idx) task_idx[t] = (uint32_t)idx;
+        } else {
+          light = true;
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, light);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long b0 = 0;
+      if (lane == leader) b0 = atomicAdd(&ctrl[kCtrlQ0], (unsigned long long)__popc(m));
+      b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
+      if (light) small_list[b0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
+    }
   }
 }
 // Slots per owner: about kItemWork lookups per item, and at least 4 lookups
 // per table entry built (each item builds N(o)'s table).
 __device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long work, uint32_t d) {
-  if (cnt == 0) return 0;
+  if (cnt == 0 || !owner_hashed(work, d)) return 0;
   const unsigned long long s1 = (work + kItemWork - 1) / kItemWork;
   const unsigned long long s2 = work / (4ull * d);
   unsigned long long s = s1 < s2 ? s1 : s2;
@@ -523,7 +550,8 @@ static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, u
 // ------------------------------------------------------------------ driver
 
 // defined in intersect.cu: warp merge over a list of edge indices
-int merge_small_edges(tc_graph* g, int mode, const uint32_t* list, uint64_t nlist,
+int merge_small_edges(tc_graph* g, int mode, const uint32_t* list,
+                      const unsigned long long* nlist_dev, uint64_t nlist_max,
                       const int64_t* ustart, uint32_t* per_edge);
 
 template <int M>
@@ -567,8 +595,9 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   TC_TRY(items0.alloc(nitems0, st));
   TC_TRY(items1.alloc(nitems1, st));
   if (ntasks > 0) {
-    launch(k_bucket_scatter<M>, grid_for((int64_t)nidx, T), T, 0, st, s, nidx, ostart.p, cursor.p,
-           descs.p, task_split.p, per_edge ? task_idx.p : (uint32_t*)nullptr);
+    launch(k_bucket_scatter<M>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx, ostart.p,
+           owner_work.p, cursor.p, descs.p, task_split.p,
+           per_edge ? task_idx.p : (uint32_t*)nullptr, small_list.p, g->ctrl.p);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
            items0.p, items1.p, counters.p);
   }
@@ -581,7 +610,10 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
       g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge, counters.p + 3)));
   cudaEventRecord(g->ev[7], st);  // end of the hash kernels
-  if (nsmall > 0) TC_TRY(merge_small_edges(g, M, small_list.p, nsmall, ustart, per_edge));
+  // the merge list: small owners (from the count pass) and light owners
+  // (appended by the scatter pass); its length is read on the device
+  if (nsmall > 0 || ntasks > 0)
+    TC_TRY(merge_small_edges(g, M, small_list.p, g->ctrl.p + kCtrlQ0, nidx, ustart, per_edge));
   return TC_OK;
 }
 

@@ -105,17 +105,20 @@ k_cover_intersect(const uint2* __restrict__ H, int64_t nh, const int64_t* __rest
 }
 
 // Edges listed by the bucketing step as having a small owner (both
-// endpoints of degree <= the small-owner bound): warp merge, list chunks
-// grabbed from *work.  mode 0 = cover (list holds H indices), 1 = plain
-// (list holds CSR entry indices with u < v).
+// endpoints of degree <= the small-owner bound, or an owner whose edges are
+// too few to pay for a hash table): warp merge, list chunks grabbed from
+// *work; the list length is read from device memory (*nlist_dev), since the
+// bucketing step appends to it on the GPU.  mode 0 = cover (list holds H
+// indices), 1 = plain (list holds CSR entry indices with u < v).
 __global__ void __launch_bounds__(kIsThreads)
-k_small_merge(int mode, const uint32_t* __restrict__ list, int64_t nlist,
+k_small_merge(int mode, const uint32_t* __restrict__ list, const unsigned long long* nlist_dev,
               const uint2* __restrict__ H, const int64_t* __restrict__ off,
               const uint32_t* __restrict__ scols, const uint4* __restrict__ seg,
               const unsigned long long* __restrict__ hoff, const uint32_t* __restrict__ erow,
               const uint32_t* __restrict__ cols, const int64_t* __restrict__ ustart,
               uint32_t* __restrict__ per_edge, unsigned long long* work, unsigned long long* ctrl) {
   const int lane = threadIdx.x & 31;
+  const int64_t nlist = (int64_t)*nlist_dev;
   unsigned long long acc = 0, elems = 0;
   while (true) {
     unsigned long long base = 0;
@@ -147,12 +150,13 @@ k_small_merge(int mode, const uint32_t* __restrict__ list, int64_t nlist,
   block_add(elems, &ctrl[kCtrlElems]);
 }
 
-int merge_small_edges(tc_graph* g, int mode, const uint32_t* list, uint64_t nlist,
+int merge_small_edges(tc_graph* g, int mode, const uint32_t* list,
+                      const unsigned long long* nlist_dev, uint64_t nlist_max,
                       const int64_t* ustart, uint32_t* per_edge) {
   cudaStream_t s = g->stream;
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
-  launch(k_small_merge, grid_for((int64_t)nlist * 32, kIsThreads, 8), kIsThreads, 0, s, mode, list,
-         (int64_t)nlist, g->cover.p, g->off, g->scols.p, g->seg.p, g->hoff.p, g->erow.p, g->cols,
+  launch(k_small_merge, grid_for((int64_t)nlist_max * 32, kIsThreads, 8), kIsThreads, 0, s, mode,
+         list, nlist_dev, g->cover.p, g->off, g->scols.p, g->seg.p, g->hoff.p, g->erow.p, g->cols,
          ustart, per_edge, g->ctrl.p + kCtrlWork, g->ctrl.p);
   TC_CUDA(cudaGetLastError());
   return TC_OK;

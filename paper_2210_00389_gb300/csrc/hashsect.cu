@@ -28,11 +28,11 @@
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
 // split into work items (owner, slot) of about kItemWork lookups; a CTA
 // takes an item, builds a bucketized hash table of N(o) in shared memory
-// (4 slots of 4 bytes per bucket, load <= 1/2, one 16-byte shared load per
-// lookup) and its warps take the item's edges from a shared counter.
+// (4 slots of 4 bytes per bucket, load <= 1/4, usually one 16-byte shared
+// load per lookup) and its warps take the item's edges from a shared counter.
 // Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (six
 // per SM); larger owners use 1024-thread CTAs with 192 KB tables.  Rows
-// longer than a table (24,576 entries) are processed in windows of
+// longer than a table (12,288 entries) are processed in windows of
 // consecutive entries (an id range); every probe run keeps a cursor across
 // windows, so each probe element is looked up once.
 #include <algorithm>
@@ -42,7 +42,7 @@
 namespace tc {
 
 constexpr uint32_t kSmallOwner = 64;              // owners this small use the merge
-constexpr uint32_t kMediumMax = 4096;             // larger owners use the big tables
+constexpr uint32_t kMediumMax = 2048;             // larger owners use the big tables
 constexpr unsigned long long kItemWork = 1ull << 19;  // target lookups per work item
 constexpr unsigned long long kBuildRatio = 4;     // hash an owner only if lookups >= 4 d(o)
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
@@ -288,14 +288,24 @@ __device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t nb, uint32_
 
 // Slots of a bucket fill in order and never empty again, so a bucket whose
 // last slot is empty ends the search.
-__device__ __forceinline__ unsigned table_find(const uint4* tab4, uint32_t nb, uint32_t w) {
+// Warp-uniform: all 32 lanes call it (valid = false on padding lanes).  One
+// bucket read per lane; a lane whose bucket is full without a match moves to
+// the next bucket, and the loop runs only while some lane still needs one.
+__device__ __forceinline__ unsigned table_find(const uint4* tab4, uint32_t nb, uint32_t w,
+                                               bool valid) {
   uint32_t b = hash_bucket(w, nb);
-  while (true) {
-    const uint4 q = tab4[b];
-    if (q.x == w || q.y == w || q.z == w || q.w == w) return 1u;
-    if (q.w == kEmpty) return 0u;
-    b = next_bucket(b, nb);
+  uint4 q = tab4[b];
+  bool hit = valid && (q.x == w || q.y == w || q.z == w || q.w == w);
+  bool more = valid && !hit && q.w != kEmpty;
+  while (__any_sync(0xFFFFFFFFu, more)) {
+    if (more) {
+      b = next_bucket(b, nb);
+      q = tab4[b];
+      hit = q.x == w || q.y == w || q.z == w || q.w == w;
+      more = !hit && q.w != kEmpty;
+    }
   }
+  return hit ? 1u : 0u;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
@@ -323,7 +333,7 @@ __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, ui
     }
 #pragma unroll
     for (int j = 0; j < kUnroll; ++j)
-      if (w[j] != kEmpty) c += table_find(tab4, nb, w[j]);
+      c += table_find(tab4, nb, w[j], w[j] != kEmpty);
   }
   return c;
 }
@@ -374,7 +384,7 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
     }
 #pragma unroll
     for (int j = 0; j < kUnroll; ++j)
-      if (e[j] != kEmpty) c += table_find(tab4, nb, e[j]);
+      c += table_find(tab4, nb, e[j], e[j] != kEmpty);
   }
   if (lane == 0) *probes += total;
   unsigned big = __ballot_sync(0xFFFFFFFFu, (uint32_t)lane < nt && !small);
@@ -410,7 +420,7 @@ __device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict_
 #pragma unroll
     for (int j = 0; j < kUnroll; ++j) {
       const bool in = w[j] <= hi;  // kEmpty > hi: padding never counts
-      if (in) c += table_find(tab4, nb, w[j]);
+      c += table_find(tab4, nb, w[j], in);
       nin += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in));
     }
     pos += nin;  // the elements <= hi form a prefix of the sorted run
@@ -429,7 +439,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  uint4* __restrict__ cursors, uint32_t* __restrict__ per_edge,
                  unsigned long long* item_counter, unsigned long long* ctrl) {
   constexpr int kWarps = THREADS / 32;
-  constexpr uint32_t kWin = 2 * BUCKETS;  // owner entries per table (load <= 1/2)
+  constexpr uint32_t kWin = BUCKETS;      // owner entries per table (load <= 1/4)
   extern __shared__ uint4 tab4[];         // BUCKETS buckets (dynamic shared memory)
   __shared__ unsigned long long s_item;
   __shared__ unsigned long long s_next;
@@ -449,7 +459,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
     const int64_t ro = off[o];
     const uint32_t d = (uint32_t)(off[o + 1] - ro);
     const uint32_t nwin = (d + kWin - 1) / kWin;
-    const uint32_t nb = nwin == 1 ? max(32u, (d + 1) / 2) : (uint32_t)BUCKETS;  // >= 2 slots/entry
+    const uint32_t nb = nwin == 1 ? max(32u, d) : (uint32_t)BUCKETS;  // >= 4 slots per entry
     for (uint32_t wdx = 0; wdx < nwin; ++wdx) {
       const uint32_t wb = wdx * kWin;
       const uint32_t we = min(d, wb + kWin);
@@ -527,7 +537,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
 // 192 KB tables (windows of 24,576 entries), one per SM.
 constexpr int kMedThreads = 256, kMedBuckets = 2048, kMedPerSM = 6;
 constexpr int kBigThreads = 1024, kBigBuckets = 12288, kBigPerSM = 1;
-static_assert(2 * kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
+static_assert(kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
 
 template <int M, int THREADS, int BUCKETS, int MINB, bool BATCH>
 static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, uint64_t nitems,

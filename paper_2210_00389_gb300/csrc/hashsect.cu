@@ -26,7 +26,7 @@
 //
 // Bucketing (a3) is a counting sort of the edges by owner.  Owners of degree
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
-// split into work items (owner, slot) of about kItemWork lookups; a CTA
+// split into work items (owner, slot) of about item_work lookups; a CTA
 // takes an item, builds a bucketized hash table of N(o) in shared memory
 // (4 slots of 4 bytes per bucket, load <= 1/4, usually one 16-byte shared
 // load per lookup) and its warps take the item's edges from a shared counter.
@@ -43,7 +43,9 @@ namespace tc {
 
 constexpr uint32_t kSmallOwner = 64;              // owners this small use the merge
 constexpr uint32_t kMediumMax = 2048;             // larger owners use the big tables
-constexpr unsigned long long kItemWork = 1ull << 19;  // target lookups per work item
+// target lookups per work item, per mode (cover, plain): tuned on R-MAT
+// scale 20/22; larger items rebuild fewer tables, smaller ones balance better
+constexpr unsigned long long kItemWork[2] = {1ull << 21, 1ull << 19};
 constexpr unsigned long long kBuildRatio = 4;     // hash an owner only if lookups >= 4 d(o)
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
@@ -201,11 +203,12 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
     }
   }
 }
-// Slots per owner: about kItemWork lookups per item, and at least 4 lookups
+// Slots per owner: about item_work lookups per item, and at least 4 lookups
 // per table entry built (each item builds N(o)'s table).
-__device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long work, uint32_t d) {
+__device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long work, uint32_t d,
+                                                unsigned long long item_work) {
   if (cnt == 0 || !owner_hashed(work, d)) return 0;
-  const unsigned long long s1 = (work + kItemWork - 1) / kItemWork;
+  const unsigned long long s1 = (work + item_work - 1) / item_work;
   const unsigned long long s2 = work / (4ull * d);
   unsigned long long s = s1 < s2 ? s1 : s2;
   const unsigned long long cap = (cnt + 3) / 4;
@@ -223,13 +226,13 @@ __device__ __forceinline__ int owner_class(uint32_t d) { return d > kMediumMax ?
 __global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
                               const uint32_t* __restrict__ owner_cnt,
                               const unsigned long long* __restrict__ owner_work,
-                              unsigned long long* ctrl) {
+                              unsigned long long item_work, unsigned long long* ctrl) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long t[2] = {0ull, 0ull};
   for (; o < (int64_t)n; o += stride) {
     const uint32_t d = degree(off, (uint32_t)o);
-    t[owner_class(d)] += owner_slots(owner_cnt[o], owner_work[o], d);
+    t[owner_class(d)] += owner_slots(owner_cnt[o], owner_work[o], d, item_work);
   }
   for (int c = 0; c < 2; ++c) {
     unsigned long long x = t[c];
@@ -242,13 +245,13 @@ __global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
 __global__ void k_item_write(const int64_t* __restrict__ off, uint32_t n,
                              const uint32_t* __restrict__ owner_cnt,
                              const unsigned long long* __restrict__ owner_work,
-                             uint2* __restrict__ items0, uint2* __restrict__ items1,
-                             unsigned long long* cursors) {
+                             unsigned long long item_work, uint2* __restrict__ items0,
+                             uint2* __restrict__ items1, unsigned long long* cursors) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; o < (int64_t)n; o += stride) {
     const uint32_t d = degree(off, (uint32_t)o);
-    const uint32_t s = owner_slots(owner_cnt[o], owner_work[o], d);
+    const uint32_t s = owner_slots(owner_cnt[o], owner_work[o], d, item_work);
     if (s == 0) continue;
     const int c = owner_class(d);
     const unsigned long long b = atomicAdd(&cursors[c], (unsigned long long)s);
@@ -590,7 +593,7 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   launch(k_u32_to_u64, grid_for(g->n, T), T, 0, st, owner_cnt.p, g->n, ostart.p);
   TC_TRY(exclusive_scan_u64(ostart.p, g->n, g->ctrl.p + kCtrlTmp, st));
   launch(k_item_counts, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-         g->ctrl.p);
+         kItemWork[M], g->ctrl.p);
   TC_CUDA(cudaGetLastError());
   TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
                           cudaMemcpyDeviceToHost, st));
@@ -609,14 +612,14 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
            owner_work.p, cursor.p, descs.p, task_split.p,
            per_edge ? task_idx.p : (uint32_t*)nullptr, small_list.p, g->ctrl.p);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-           items0.p, items1.p, counters.p);
+           kItemWork[M], items0.p, items1.p, counters.p);
   }
   TC_CUDA(cudaGetLastError());
   cudaEventRecord(g->ev[6], st);  // end of bucketing
   TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigPerSM, false>(
       g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge, counters.p + 2)));
-  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedPerSM, true>(
+  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedPerSM, false>(
       g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge, counters.p + 3)));
   cudaEventRecord(g->ev[7], st);  // end of the hash kernels

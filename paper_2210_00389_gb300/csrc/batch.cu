@@ -1,29 +1,407 @@
 // Batched counting of many independent graphs (tc_count_batch).
-// Preliminary form: one graph object per input, counted in turn on the
-// caller's stream.
+//
+// One persistent kernel: every CTA takes graphs from a global queue (largest
+// first) and runs the whole method on each within the block, with its
+// per-graph arrays in a per-CTA slice of one scratch arena:
+//   checks   offsets monotone and ending at nnz; columns < n, rows strictly
+//            ascending, no self-loops (a failing graph gets
+//            TC_ERR_INVALID_GRAPH and is skipped);
+//   roots    maximum-degree vertex (lowest id on ties), and the lowest id of
+//            every other component (union-find with min-id roots), as in
+//            Def. 2 / Alg. 1 of Bader et al., "Triangle Counting Through
+//            Cover-Edges";
+//   levels   one multi-source, level-synchronous BFS inside the block;
+//   count    for every cover edge (u, v) (Thm. 1: L(u) = L(v), u < v) the
+//            common neighbours w with L(w) != L(u) or w > v (Alg. 1 /
+//            Thm. 2), by warp merge; plain mode counts every edge u < v with
+//            apexes w > v;
+//   reduce   warp shuffles, then one 64-bit store per graph.
+// There is no host synchronisation per BFS level or per graph.  The launch
+// is captured into a CUDA graph on an internal stream and replayed on the
+// caller's stream.  Graphs with more than kBatchMaxN vertices take the
+// single-graph path instead.
+#include <algorithm>
+#include <numeric>
 #include <vector>
 
 #include "internal.cuh"
+#include "warp_isect.cuh"
+
+namespace tc {
+
+constexpr uint32_t kBatchMaxN = 1u << 16;  // vertices per graph in the batch kernel
+
+struct BGraph {
+  const int64_t* off;
+  const uint32_t* cols;
+  uint32_t n;
+  uint32_t pad;
+  int64_t nnz;
+};
+
+__device__ __forceinline__ uint32_t bfind(uint32_t* P, uint32_t x) {
+  while (true) {
+    const uint32_t p = *reinterpret_cast<volatile uint32_t*>(&P[x]);
+    if (p == x) return x;
+    const uint32_t gp = *reinterpret_cast<volatile uint32_t*>(&P[p]);
+    if (gp == p) return p;
+    P[x] = gp;  // path halving; parents only ever point to smaller ids
+    x = gp;
+  }
+}
+
+struct CoverPred {
+  const uint32_t* L;
+  uint32_t lvl, v;
+  __device__ __forceinline__ bool operator()(uint32_t w) const { return L[w] != lvl || w > v; }
+};
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_batch(const BGraph* __restrict__ graphs, const uint32_t* __restrict__ order, int32_t ngraphs,
+        int mode, uint32_t* __restrict__ scratch, uint32_t slot_n,
+        unsigned long long* __restrict__ counts, int* __restrict__ status,
+        unsigned long long* queue) {
+  constexpr int kWarps = THREADS / 32;
+  __shared__ int s_idx;
+  __shared__ unsigned long long s_key;
+  __shared__ uint32_t s_qn;
+  __shared__ unsigned long long s_red[kWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* L = scratch + (size_t)blockIdx.x * 4 * slot_n;
+  uint32_t* P = L + slot_n;
+  uint32_t* qa = P + slot_n;
+  uint32_t* qb = qa + slot_n;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_idx = (int)atomicAdd(queue, 1ull);
+      s_key = 0;
+      s_qn = 0;
+    }
+    __syncthreads();
+    const int qi = s_idx;
+    if (qi >= ngraphs) break;
+    const int gi = (int)order[qi];
+    const BGraph G = graphs[gi];
+    const uint32_t n = G.n;
+    const int64_t* off = G.off;
+    const uint32_t* cols = G.cols;
+    // -- checks: offsets first (they bound every later access)
+    bool bad = false;
+    for (uint32_t v = threadIdx.x; v <= n; v += THREADS) {
+      const int64_t o = off[v];
+      if (o < 0 || o > G.nnz || (v == 0 && o != 0) || (v == n && o != G.nnz)) bad = true;
+      else if (v < n && off[v + 1] < o) bad = true;
+    }
+    if (__syncthreads_or(bad)) {
+      if (threadIdx.x == 0) { status[gi] = TC_ERR_INVALID_GRAPH; counts[gi] = 0; }
+      continue;
+    }
+    for (uint32_t v = wid; v < n; v += kWarps) {
+      const int64_t b = off[v], e = off[v + 1];
+      for (int64_t i = b + lane; i < e; i += 32) {
+        const uint32_t w = cols[i];
+        if (w >= n || w == v || (i > b && cols[i - 1] >= w)) bad = true;
+      }
+      const unsigned long long d = (unsigned long long)(e - b);
+      if (lane == 0) atomicMax(&s_key, (d << 32) | (0xFFFFFFFFull - v));
+    }
+    if (__syncthreads_or(bad)) {
+      if (threadIdx.x == 0) { status[gi] = TC_ERR_INVALID_GRAPH; counts[gi] = 0; }
+      continue;
+    }
+    const uint32_t r0 = n > 0 ? 0xFFFFFFFFu - (uint32_t)(s_key & 0xFFFFFFFFull) : 0u;
+    // -- components: parents point to smaller ids, so every root is its
+    //    component's minimum
+    for (uint32_t v = threadIdx.x; v < n; v += THREADS) {
+      const int64_t b = off[v];
+      const uint32_t f = off[v + 1] > b ? cols[b] : v;
+      P[v] = f < v ? f : v;
+    }
+    __syncthreads();
+    for (uint32_t v = wid; v < n; v += kWarps) {
+      const int64_t b = off[v], e = off[v + 1];
+      for (int64_t i = b + lane; i < e; i += 32) {
+        uint32_t x = v, y = cols[i];
+        if (y >= x) continue;
+        while (true) {
+          x = bfind(P, x);
+          y = bfind(P, y);
+          if (x == y) break;
+          if (x < y) { const uint32_t t = x; x = y; y = t; }
+          if (atomicCAS(&P[x], x, y) == x) break;
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t v = threadIdx.x; v < n; v += THREADS) P[v] = bfind(P, v);
+    __syncthreads();
+    // -- level 0: r0 and the lowest id of every other component
+    const uint32_t c0 = n > 0 ? P[r0] : 0u;
+    for (uint32_t v = threadIdx.x; v < n; v += THREADS) {
+      const bool root = v == r0 || (P[v] == v && v != c0);
+      L[v] = root ? 0u : kUnvisited;
+      if (root && off[v + 1] > off[v]) qa[atomicAdd(&s_qn, 1u)] = v;
+    }
+    __syncthreads();
+    // -- level-synchronous BFS, top-down, frontier queues in scratch
+    uint32_t qn = s_qn;
+    uint32_t cur = 0;
+    while (qn > 0) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_qn = 0;
+      __syncthreads();
+      for (uint32_t k = wid; k < qn; k += kWarps) {
+        const uint32_t x = qa[k];
+        const int64_t b = off[x], e = off[x + 1];
+        for (int64_t i = b + lane; i < e; i += 32) {
+          const uint32_t y = cols[i];
+          if (L[y] == kUnvisited && atomicCAS(&L[y], kUnvisited, cur + 1) == kUnvisited)
+            qb[atomicAdd(&s_qn, 1u)] = y;
+        }
+      }
+      __syncthreads();
+      qn = s_qn;
+      uint32_t* t = qa; qa = qb; qb = t;
+      ++cur;
+    }
+    __syncthreads();
+    // -- counting: warp per vertex u, cover edges (or all edges u < v)
+    unsigned long long acc = 0;
+    for (uint32_t u = wid; u < n; u += kWarps) {
+      const int64_t b = off[u], e = off[u + 1];
+      const uint32_t lvl = L[u];
+      for (int64_t base = b; base < e; base += 32) {
+        const int64_t i = base + lane;
+        bool cand = false;
+        uint32_t v = 0;
+        if (i < e) {
+          v = cols[i];
+          cand = v > u && (mode == TC_MODE_PLAIN || L[v] == lvl);
+        }
+        unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+        while (m) {
+          const int j = __ffs(m) - 1;
+          m &= m - 1;
+          const uint32_t vv = __shfl_sync(0xFFFFFFFFu, v, j);
+          const int64_t bv = off[vv], ev = off[vv + 1];
+          if (mode == TC_MODE_COVER) {
+            acc += warp_intersect_if(cols + b, e - b, cols + bv, ev - bv, CoverPred{L, lvl, vv});
+          } else {
+            // neighbours above vv: after entry (base + j) in u's row, and
+            // after vv's own position in its row
+            int64_t lo = bv, hi = ev;
+            while (lo < hi) {
+              const int64_t mid = (lo + hi) >> 1;
+              if (cols[mid] <= vv) lo = mid + 1; else hi = mid;
+            }
+            const int64_t au = base + j + 1;
+            acc += warp_intersect(cols + au, e - au, cols + lo, ev - lo);
+          }
+        }
+      }
+    }
+    // -- reduction to one count per graph
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0) s_red[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < kWarps; ++w) t += s_red[w];
+      counts[gi] = t;
+      status[gi] = TC_OK;
+    }
+  }
+}
+
+template <int THREADS>
+static void launch_batch(int grid, cudaStream_t s, const BGraph* graphs, const uint32_t* order,
+                         int32_t ng, int mode, uint32_t* scratch, uint32_t slot_n,
+                         unsigned long long* counts, int* status, unsigned long long* queue) {
+  launch(k_batch<THREADS>, grid, THREADS, 0, s, graphs, order, ng, mode, scratch, slot_n, counts,
+         status, queue);
+}
+
+}  // namespace tc
 
 using namespace tc;
 
 extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mode,
                               const tc_options* opt, void* cuda_stream, uint64_t* counts_out,
                               int* status_out) {
-  (void)opt;
   if (ngraphs < 0 || (ngraphs > 0 && (!graphs || !counts_out)))
     return fail(TC_ERR_INVALID_ARG, "tc_count_batch: bad arguments");
   if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
     return fail(TC_ERR_INVALID_ARG, "tc_count_batch: unknown mode %d", mode);
+  if (ngraphs == 0) return TC_OK;
+  int threads = opt && opt->block_threads > 0 ? opt->block_threads : 256;
+  int per_sm = opt && opt->blocks_per_sm > 0 ? opt->blocks_per_sm : 4;
+  if (threads != 128 && threads != 256 && threads != 512)
+    return fail(TC_ERR_INVALID_ARG, "tc_count_batch: block_threads must be 128, 256 or 512");
+  if (per_sm > 16) per_sm = 16;
+  cudaStream_t user = (cudaStream_t)cuda_stream;
+
+  // split: graphs the batch kernel takes, and large ones for the single-graph path
+  std::vector<int32_t> small, large;
   for (int32_t i = 0; i < ngraphs; ++i) {
+    const tc_csr_view& v = graphs[i];
+    if (!v.offsets || v.nnz < 0 || (v.nnz > 0 && !v.cols))
+      return fail(TC_ERR_INVALID_ARG, "tc_count_batch: graph %d has NULL arrays or nnz < 0", i);
+    (v.n <= kBatchMaxN ? small : large).push_back(i);
+  }
+  std::vector<int> st_host((size_t)ngraphs, TC_OK);
+  std::vector<unsigned long long> cnt_host((size_t)ngraphs, 0ull);
+
+  if (!small.empty()) {
+    // descriptors: device views are used in place; host views are packed
+    // into one pinned arena and copied with a single transfer
+    size_t host_bytes = 0;
+    uint32_t max_n = 1;
+    for (int32_t i : small) {
+      const tc_csr_view& v = graphs[i];
+      max_n = std::max(max_n, v.n + 1);
+      if (!(v.on_device && is_device_ptr(v.offsets))) {
+        host_bytes += sizeof(int64_t) * ((size_t)v.n + 1);
+        host_bytes = (host_bytes + 15) & ~(size_t)15;
+        host_bytes += sizeof(uint32_t) * (size_t)v.nnz;
+        host_bytes = (host_bytes + 15) & ~(size_t)15;
+      }
+    }
+    cudaStream_t cs = nullptr;
+    TC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = TC_OK;
+    unsigned char* pinned = nullptr;
+    DevBuf<unsigned char> arena;
+    DevBuf<BGraph> dgraphs;
+    DevBuf<uint32_t> dorder, scratch;
+    DevBuf<unsigned long long> dcounts, dqueue;
+    DevBuf<int> dstatus;
+    cudaGraph_t cg = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    do {
+      std::vector<BGraph> hg(small.size());
+      if (host_bytes > 0) {
+        if (cudaMallocHost(&pinned, host_bytes) != cudaSuccess) {
+          cudaGetLastError();
+          rc = fail(TC_ERR_OOM, "tc_count_batch: pinned staging of %zu bytes failed", host_bytes);
+          break;
+        }
+        if ((rc = arena.alloc(host_bytes, cs)) != TC_OK) break;
+      }
+      size_t pos = 0;
+      for (size_t k = 0; k < small.size(); ++k) {
+        const tc_csr_view& v = graphs[small[k]];
+        BGraph b{};
+        b.n = v.n;
+        b.nnz = v.nnz;
+        if (v.on_device && is_device_ptr(v.offsets)) {
+          b.off = v.offsets;
+          b.cols = v.cols;
+        } else {
+          const size_t ob = sizeof(int64_t) * ((size_t)v.n + 1);
+          memcpy(pinned + pos, v.offsets, ob);
+          b.off = reinterpret_cast<const int64_t*>(arena.p + pos);
+          pos = (pos + ob + 15) & ~(size_t)15;
+          const size_t cb = sizeof(uint32_t) * (size_t)v.nnz;
+          if (cb) memcpy(pinned + pos, v.cols, cb);
+          b.cols = reinterpret_cast<const uint32_t*>(arena.p + pos);
+          pos = (pos + cb + 15) & ~(size_t)15;
+        }
+        hg[k] = b;
+      }
+      // largest graphs first
+      std::vector<uint32_t> ord(small.size());
+      std::iota(ord.begin(), ord.end(), 0u);
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](uint32_t a, uint32_t b) { return hg[a].nnz > hg[b].nnz; });
+      const int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, (int64_t)small.size());
+      if ((rc = dgraphs.alloc(hg.size(), cs)) != TC_OK) break;
+      if ((rc = dorder.alloc(ord.size(), cs)) != TC_OK) break;
+      if ((rc = dcounts.alloc(hg.size(), cs)) != TC_OK) break;
+      if ((rc = dstatus.alloc(hg.size(), cs)) != TC_OK) break;
+      if ((rc = dqueue.alloc(1, cs)) != TC_OK) break;
+      if ((rc = scratch.alloc((size_t)grid * 4 * max_n, cs)) != TC_OK) break;
+      cudaError_t e = cudaSuccess;
+      if (host_bytes > 0)
+        e = cudaMemcpyAsync(arena.p, pinned, host_bytes, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dgraphs.p, hg.data(), sizeof(BGraph) * hg.size(),
+                            cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dorder.p, ord.data(), sizeof(uint32_t) * ord.size(),
+                            cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "batch upload", __FILE__, __LINE__); break; }
+      // capture: reset the queue, one persistent launch
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__); break; }
+      cudaMemsetAsync(dqueue.p, 0, sizeof(unsigned long long), cs);
+      const int32_t ng = (int32_t)small.size();
+      if (threads == 128)
+        launch_batch<128>(grid, cs, dgraphs.p, dorder.p, ng, mode, scratch.p, max_n, dcounts.p,
+                          dstatus.p, dqueue.p);
+      else if (threads == 256)
+        launch_batch<256>(grid, cs, dgraphs.p, dorder.p, ng, mode, scratch.p, max_n, dcounts.p,
+                          dstatus.p, dqueue.p);
+      else
+        launch_batch<512>(grid, cs, dgraphs.p, dorder.p, ng, mode, scratch.p, max_n, dcounts.p,
+                          dstatus.p, dqueue.p);
+      e = cudaStreamEndCapture(cs, &cg);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }
+      e = cudaGraphInstantiate(&exec, cg, 0);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); break; }
+      // replay on the caller's stream, ordered after the uploads
+      if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) == cudaSuccess &&
+          (e = cudaEventRecord(done, cs)) == cudaSuccess &&
+          (e = cudaStreamWaitEvent(user, done, 0)) == cudaSuccess &&
+          (e = cudaGraphLaunch(exec, user)) == cudaSuccess &&
+          (e = cudaStreamSynchronize(user)) == cudaSuccess) {
+        std::vector<unsigned long long> c(hg.size());
+        std::vector<int> s(hg.size());
+        e = cudaMemcpy(c.data(), dcounts.p, sizeof(unsigned long long) * c.size(),
+                       cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+          e = cudaMemcpy(s.data(), dstatus.p, sizeof(int) * s.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+          for (size_t k = 0; k < small.size(); ++k) {
+            cnt_host[small[k]] = c[k];
+            st_host[small[k]] = s[k];
+          }
+        }
+      }
+      if (e != cudaSuccess) { rc = cuda_fail(e, "batch launch", __FILE__, __LINE__); break; }
+    } while (0);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cg) cudaGraphDestroy(cg);
+    if (done) cudaEventDestroy(done);
+    cudaStreamSynchronize(cs);
+    arena.release();
+    dgraphs.release();
+    dorder.release();
+    scratch.release();
+    dcounts.release();
+    dqueue.release();
+    dstatus.release();
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+    if (pinned) cudaFreeHost(pinned);
+    if (rc != TC_OK) return rc;
+  }
+  // graphs too large for one CTA: the single-graph path
+  for (int32_t i : large) {
     tc_graph* g = nullptr;
-    int st = tc_graph_create(&graphs[i], 0, cuda_stream, &g);
+    int st = tc_graph_create(&graphs[i], TC_GRAPH_VALIDATE, cuda_stream, &g);
     uint64_t c = 0;
     if (st == TC_OK) st = tc_count(g, mode, &c);
     tc_graph_destroy(g);
-    counts_out[i] = st == TC_OK ? c : 0;
-    if (status_out) status_out[i] = st;
     if (st != TC_OK && st != TC_ERR_INVALID_GRAPH) return st;
+    cnt_host[i] = st == TC_OK ? c : 0;
+    st_host[i] = st;
+  }
+  for (int32_t i = 0; i < ngraphs; ++i) {
+    counts_out[i] = cnt_host[i];
+    if (status_out) status_out[i] = st_host[i];
   }
   return TC_OK;
 }

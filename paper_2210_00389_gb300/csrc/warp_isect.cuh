@@ -9,10 +9,17 @@ namespace tc {
 constexpr uint32_t kInf = 0xFFFFFFFFu;  // never a vertex id (n < 2^32 - 1)
 constexpr int64_t kSkew = 24;           // merge when max(len) <= kSkew * min(len)
 
-// |A ∩ B| for strictly ascending A[0..la), B[0..lb).  All 32 lanes call it
-// with identical arguments; each returns its share of the count.
-__device__ __forceinline__ unsigned warp_intersect(const uint32_t* __restrict__ A, int64_t la,
-                                                   const uint32_t* __restrict__ B, int64_t lb) {
+struct AcceptAll {
+  __device__ __forceinline__ bool operator()(uint32_t) const { return true; }
+};
+
+// Number of w in A ∩ B with pred(w), for strictly ascending A[0..la),
+// B[0..lb).  All 32 lanes call it with identical arguments; each returns
+// its share of the count.
+template <class Pred>
+__device__ __forceinline__ unsigned warp_intersect_if(const uint32_t* __restrict__ A, int64_t la,
+                                                      const uint32_t* __restrict__ B, int64_t lb,
+                                                      Pred pred) {
   const int lane = threadIdx.x & 31;
   if (la > lb) {
     const uint32_t* t = A; A = B; B = t;
@@ -31,7 +38,7 @@ __device__ __forceinline__ unsigned warp_intersect(const uint32_t* __restrict__ 
         const int64_t mid = (lo + hi) >> 1;
         if (__ldg(B + mid) < x) lo = mid + 1; else hi = mid;
       }
-      if (lo < lb && __ldg(B + lo) == x) ++cnt;
+      if (lo < lb && __ldg(B + lo) == x && pred(x)) ++cnt;
     }
     return cnt;
   }
@@ -52,7 +59,7 @@ __device__ __forceinline__ unsigned warp_intersect(const uint32_t* __restrict__ 
       if (bv < a) pos += s;
     }
     const uint32_t bv = __shfl_sync(0xFFFFFFFFu, b, pos);
-    if (lane <= a_last && bv == a) ++cnt;
+    if (lane <= a_last && bv == a && pred(a)) ++cnt;
     const bool adv_a = amax <= bmax, adv_b = bmax <= amax;
     if (adv_a) {
       ia += 32;
@@ -66,6 +73,12 @@ __device__ __forceinline__ unsigned warp_intersect(const uint32_t* __restrict__ 
     }
   }
   return cnt;
+}
+
+// |A ∩ B| (every common element counts).
+__device__ __forceinline__ unsigned warp_intersect(const uint32_t* __restrict__ A, int64_t la,
+                                                   const uint32_t* __restrict__ B, int64_t lb) {
+  return warp_intersect_if(A, la, B, lb, AcceptAll());
 }
 
 }  // namespace tc

@@ -1,0 +1,91 @@
+"""tc_count_batch against the CPU oracle: every graph's count exact, alone or
+in a mix, for every block shape; invalid graphs flagged; graphs too large
+for the batch kernel take the single-graph path."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+    torch.cuda.init()
+    import paper_2210_00389_gb300 as tc
+    return tc
+
+
+def mixed_graphs():
+    gs = [c[0] for c in pins.closed_form_cases()]
+    gs += pins.random_small_graphs()
+    gs += [gg.rmat(s, ef, seed=500 + s + ef, relabel_seed=(600 + s) if s % 2 else None)
+           for s, ef in ((6, 8), (8, 16), (10, 32), (11, 8), (12, 16))]
+    gs += [gg.erdos_renyi(300, 10 / 299, 71), gg.complete(25), gg.complete(120)]
+    gs += [gg.chung_lu_islands(1 << 12, mean_degree=8, cap=256, seed=9)]
+    return gs
+
+
+def expected(g):
+    return oracle.cetc(g)["T"]
+
+
+def test_batch_mixed_host_views(tc):
+    gs = mixed_graphs()
+    want = [expected(g) for g in gs]
+    for mode in (tc.TC_MODE_COVER, tc.TC_MODE_PLAIN):
+        counts, status = tc.tc_count_batch([(g.offsets, g.cols) for g in gs], mode)
+        assert (status == tc.TC_OK).all()
+        assert counts.tolist() == want
+
+
+@pytest.mark.parametrize("threads,per_sm", [(128, 8), (256, 4), (512, 2), (256, 1)])
+def test_batch_block_shapes(tc, threads, per_sm):
+    gs = mixed_graphs()
+    want = [expected(g) for g in gs]
+    opt = tc.Options(0, 0, threads, per_sm)
+    counts, status = tc.tc_count_batch([(g.offsets, g.cols) for g in gs], tc.TC_MODE_COVER, opt)
+    assert (status == tc.TC_OK).all()
+    assert counts.tolist() == want
+
+
+def test_batch_device_views_and_alone_vs_mix(tc):
+    import torch
+    gs = mixed_graphs()
+    dev = [(torch.from_numpy(g.offsets).cuda(), torch.from_numpy(g.cols).cuda()) for g in gs]
+    mix, st = tc.tc_count_batch(dev, tc.TC_MODE_COVER)
+    assert (st == tc.TC_OK).all()
+    for i in (0, 5, len(gs) - 1):
+        alone, st1 = tc.tc_count_batch([dev[i]], tc.TC_MODE_COVER)
+        assert st1[0] == tc.TC_OK and alone[0] == mix[i] == expected(gs[i])
+
+
+def test_batch_invalid_and_large(tc):
+    good = gg.complete(6)
+    bad_cols = good.cols.copy()
+    bad_cols[3] = 77                      # column out of range
+    unsorted = good.cols.copy()
+    unsorted[0], unsorted[1] = unsorted[1], unsorted[0]
+    bad_off = good.offsets.copy()
+    bad_off[2] = bad_off[3] + 1           # offsets not monotone
+    large = gg.rmat(17, 4, seed=3)        # n = 131072 > the batch kernel's limit
+    items = [(good.offsets, good.cols), (good.offsets, bad_cols), (good.offsets, unsorted),
+             (bad_off, good.cols), (large.offsets, large.cols), (good.offsets, good.cols)]
+    counts, status = tc.tc_count_batch(items, tc.TC_MODE_COVER)
+    assert status.tolist() == [tc.TC_OK, tc.TC_ERR_INVALID_GRAPH, tc.TC_ERR_INVALID_GRAPH,
+                               tc.TC_ERR_INVALID_GRAPH, tc.TC_OK, tc.TC_OK]
+    assert counts[0] == counts[5] == 20
+    assert counts[4] == oracle.plain_count(large)
+
+
+def test_batch_mixed_recipe_sample(tc):
+    """A sample of the 4,096-graph mixed recipe (R-MAT scale 6-14, Erdos-Renyi,
+    complete graphs): the first 160 graphs, every count against the oracle."""
+    specs = gg.mixed_graph_specs(4096, seed=3)[:160]
+    gs = [gg.graph_from_spec(s) for s in specs]
+    counts, status = tc.tc_count_batch([(g.offsets, g.cols) for g in gs], tc.TC_MODE_COVER)
+    assert (status == tc.TC_OK).all()
+    assert counts.tolist() == [expected(g) for g in gs]

@@ -203,13 +203,14 @@ TC_API int tc_count_plain_static(const int64_t* offsets, const uint32_t* cols, u
                                  int64_t nnz, uint64_t* count_out, void* cuda_stream);
 
 /* ---------------------------------------------------------------- batch */
-/* Tunables of the intersection (NULL anywhere = built-in / autotuned). */
+/* Tunables of the batched kernel (NULL = built-in defaults; the Python
+ * binding passes the table written by its autotuner). */
 typedef struct {
-  int32_t small_max;       /* longer list <= small_max: sub-warp merge bucket */
-  int32_t hub_min;         /* owner degree >= hub_min: hub (shared-memory) bucket */
-  int32_t block_threads;   /* threads per block of the persistent batch kernel */
-  int32_t blocks_per_sm;   /* resident blocks per SM of the persistent kernel */
-  int32_t reserved[4];
+  int32_t block_threads;   /* threads per block of the persistent batch kernel: 128, 256, 512 */
+  int32_t blocks_per_sm;   /* resident blocks per SM (1..16) */
+  int32_t skew;            /* warp merge when the longer list is <= skew x the shorter,
+                              else binary search of the shorter in the longer (>= 2) */
+  int32_t reserved[5];
 } tc_options;
 
 /* Count ngraphs independent graphs in one persistent, CUDA-graph-captured

@@ -71,9 +71,8 @@ class Stats(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("small_max", ctypes.c_int32), ("hub_min", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("skew", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -299,8 +298,22 @@ def tc_count_plain_static(offsets, cols, count_out, n: int | None = None, stream
            "tc_count_plain_static")
 
 
+def autotuned_options() -> Options | None:
+    """The batched kernel's setting chosen by autotune.py (None if absent)."""
+    path = os.path.join(_HERE, "autotune.json")
+    try:
+        import json
+        b = json.load(open(path))["batch"]
+        return Options(int(b["block_threads"]), int(b["blocks_per_sm"]), int(b["skew"]))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def tc_count_batch(graphs, mode: int = TC_MODE_COVER, opt: Options | None = None, stream=None):
-    """Count a list of (offsets, cols) CSRs; returns (counts uint64[], status int32[])."""
+    """Count a list of (offsets, cols) CSRs; returns (counts uint64[], status int32[]).
+    Without ``opt`` the autotuned setting is used when autotune.json exists."""
+    if opt is None:
+        opt = autotuned_options()
     k = len(graphs)
     views = (CSRView * max(k, 1))()
     for i, (off, cols) in enumerate(graphs):

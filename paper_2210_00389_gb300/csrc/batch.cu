@@ -59,7 +59,7 @@ struct CoverPred {
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_batch(const BGraph* __restrict__ graphs, const uint32_t* __restrict__ order, int32_t ngraphs,
-        int mode, uint32_t* __restrict__ scratch, uint32_t slot_n,
+        int mode, int64_t skew, uint32_t* __restrict__ scratch, uint32_t slot_n,
         unsigned long long* __restrict__ counts, int* __restrict__ status,
         unsigned long long* queue) {
   constexpr int kWarps = THREADS / 32;
@@ -186,7 +186,8 @@ k_batch(const BGraph* __restrict__ graphs, const uint32_t* __restrict__ order, i
           const uint32_t vv = __shfl_sync(0xFFFFFFFFu, v, j);
           const int64_t bv = off[vv], ev = off[vv + 1];
           if (mode == TC_MODE_COVER) {
-            acc += warp_intersect_if(cols + b, e - b, cols + bv, ev - bv, CoverPred{L, lvl, vv});
+            acc += warp_intersect_if(cols + b, e - b, cols + bv, ev - bv, CoverPred{L, lvl, vv},
+                                     skew);
           } else {
             // neighbours above vv: after entry (base + j) in u's row, and
             // after vv's own position in its row
@@ -196,7 +197,7 @@ k_batch(const BGraph* __restrict__ graphs, const uint32_t* __restrict__ order, i
               if (cols[mid] <= vv) lo = mid + 1; else hi = mid;
             }
             const int64_t au = base + j + 1;
-            acc += warp_intersect(cols + au, e - au, cols + lo, ev - lo);
+            acc += warp_intersect_if(cols + au, e - au, cols + lo, ev - lo, AcceptAll(), skew);
           }
         }
       }
@@ -216,10 +217,10 @@ k_batch(const BGraph* __restrict__ graphs, const uint32_t* __restrict__ order, i
 
 template <int THREADS>
 static void launch_batch(int grid, cudaStream_t s, const BGraph* graphs, const uint32_t* order,
-                         int32_t ng, int mode, uint32_t* scratch, uint32_t slot_n,
+                         int32_t ng, int mode, int64_t skew, uint32_t* scratch, uint32_t slot_n,
                          unsigned long long* counts, int* status, unsigned long long* queue) {
-  launch(k_batch<THREADS>, grid, THREADS, 0, s, graphs, order, ng, mode, scratch, slot_n, counts,
-         status, queue);
+  launch(k_batch<THREADS>, grid, THREADS, 0, s, graphs, order, ng, mode, skew, scratch, slot_n,
+         counts, status, queue);
 }
 
 }  // namespace tc
@@ -239,6 +240,7 @@ extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mo
   if (threads != 128 && threads != 256 && threads != 512)
     return fail(TC_ERR_INVALID_ARG, "tc_count_batch: block_threads must be 128, 256 or 512");
   if (per_sm > 16) per_sm = 16;
+  const int64_t skew = opt && opt->skew >= 2 ? opt->skew : kSkew;
   cudaStream_t user = (cudaStream_t)cuda_stream;
 
   // split: graphs the batch kernel takes, and large ones for the single-graph path
@@ -339,13 +341,13 @@ extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mo
       cudaMemsetAsync(dqueue.p, 0, sizeof(unsigned long long), cs);
       const int32_t ng = (int32_t)small.size();
       if (threads == 128)
-        launch_batch<128>(grid, cs, dgraphs.p, dorder.p, ng, mode, scratch.p, max_n, dcounts.p,
+        launch_batch<128>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
                           dstatus.p, dqueue.p);
       else if (threads == 256)
-        launch_batch<256>(grid, cs, dgraphs.p, dorder.p, ng, mode, scratch.p, max_n, dcounts.p,
+        launch_batch<256>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
                           dstatus.p, dqueue.p);
       else
-        launch_batch<512>(grid, cs, dgraphs.p, dorder.p, ng, mode, scratch.p, max_n, dcounts.p,
+        launch_batch<512>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
                           dstatus.p, dqueue.p);
       e = cudaStreamEndCapture(cs, &cg);
       if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }

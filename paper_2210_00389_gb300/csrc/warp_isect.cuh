@@ -14,12 +14,13 @@ struct AcceptAll {
 };
 
 // Number of w in A ∩ B with pred(w), for strictly ascending A[0..la),
-// B[0..lb).  All 32 lanes call it with identical arguments; each returns
-// its share of the count.
+// B[0..lb): a windowed merge when lb <= skew * la, else a binary search of
+// the shorter list in the longer.  All 32 lanes call it with identical
+// arguments; each returns its share of the count.
 template <class Pred>
 __device__ __forceinline__ unsigned warp_intersect_if(const uint32_t* __restrict__ A, int64_t la,
                                                       const uint32_t* __restrict__ B, int64_t lb,
-                                                      Pred pred) {
+                                                      Pred pred, int64_t skew = kSkew) {
   const int lane = threadIdx.x & 31;
   if (la > lb) {
     const uint32_t* t = A; A = B; B = t;
@@ -27,7 +28,7 @@ __device__ __forceinline__ unsigned warp_intersect_if(const uint32_t* __restrict
   }
   if (la == 0) return 0;
   unsigned cnt = 0;
-  if (lb > kSkew * la) {
+  if (lb > skew * la) {
     // skewed: every lane binary-searches its elements of A in B; a lane's
     // elements increase, so its search window starts where the last ended
     int64_t lo = 0;

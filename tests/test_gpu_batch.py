@@ -46,7 +46,7 @@ def test_batch_mixed_host_views(tc):
 def test_batch_block_shapes(tc, threads, per_sm):
     gs = mixed_graphs()
     want = [expected(g) for g in gs]
-    opt = tc.Options(0, 0, threads, per_sm)
+    opt = tc.Options(threads, per_sm, 0)
     counts, status = tc.tc_count_batch([(g.offsets, g.cols) for g in gs], tc.TC_MODE_COVER, opt)
     assert (status == tc.TC_OK).all()
     assert counts.tolist() == want

@@ -223,25 +223,48 @@ TC_API int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mode,
                    int* status_out);
 
 /* ---------------------------------------------------------------- serving */
+/* A request loop on the current device (no paper counterpart: a systems form
+ * of Alg. 1).  Requests are admitted in arrival order while fewer than
+ * `slots` are in flight and their estimated device bytes fit the budget next
+ * to the resident graphs.  Admitted small one-shot graphs (n <= 65,536,
+ * nnz <= 2^20) are grouped and counted together with tc_count_batch each time
+ * the batch worker is free (continuous batching); resident and large
+ * requests run on worker threads with their own streams, so requests overlap
+ * on the device.  Counts are the same exact integers as tc_count's. */
 typedef struct tc_server tc_server;
 typedef struct {
   size_t hbm_budget_bytes; /* admission limit for resident + in-flight graphs */
-  int32_t slots;           /* max requests in flight on the device */
-  int32_t queue_capacity;  /* max queued (not yet admitted) requests */
-  int32_t wait_limit_ms;   /* bound on any internal wait (0 = 10000) */
-  int32_t reserved[4];
+  int32_t slots;           /* max requests in flight on the device (> 0) */
+  int32_t queue_capacity;  /* max queued, not yet admitted requests (<= 0: 4096) */
+  int32_t wait_limit_ms;   /* a request not admitted within this time finishes
+                              with TC_ERR_TIMEOUT (<= 0: 10000) */
+  int32_t reserved[4];     /* reserved[0] = k > 0: test hook, the k-th admitted
+                              request fails with TC_ERR_OOM as if its device
+                              allocation had failed; others must be 0 */
 } tc_serve_config;
 
+/* Start the scheduler and worker threads.  TC_ERR_INVALID_ARG for a NULL
+ * or non-positive budget / slots. */
 TC_API int tc_serve_create(const tc_serve_config* cfg, tc_server** out);
-/* Upload a graph that stays resident (CSR + levels + cover edges cached);
- * *graph_id names it in later submits. */
+/* Upload a graph that stays resident: its CSR (host or device view, copied),
+ * BFS levels and cover edges are computed now and reused by every request
+ * on *graph_id.  TC_ERR_OOM if it does not fit the budget; CSR errors as
+ * tc_graph_create with TC_GRAPH_VALIDATE. */
 TC_API int tc_serve_register(tc_server* s, const tc_csr_view* csr, uint64_t* graph_id);
-/* Queue a count request: either a resident graph (csr_or_null == NULL) or a
- * one-shot CSR (copied before return).  TC_ERR_AGAIN when the queue is full. */
+/* Queue a count request (mode TC_MODE_COVER or TC_MODE_PLAIN) on a resident
+ * graph (csr_or_null == NULL) or on a one-shot CSR (host or device view,
+ * copied before return, so the caller's buffers are free afterwards).
+ * Errors: TC_ERR_AGAIN (queue full), TC_ERR_OOM (the request alone exceeds
+ * the budget), TC_ERR_NOT_FOUND (unknown graph id), TC_ERR_CANCELLED
+ * (shutting down), TC_ERR_INVALID_ARG. */
 TC_API int tc_serve_submit(tc_server* s, const tc_csr_view* csr_or_null, uint64_t graph_id,
                     int mode, uint64_t* ticket);
-/* Non-blocking: *done = 1 when the request finished, with its count and status. */
+/* Non-blocking: *done = 1 when the request finished, then *count and
+ * *status (TC_OK, TC_ERR_INVALID_GRAPH, TC_ERR_TIMEOUT, TC_ERR_OOM, ...) are
+ * set and the ticket is forgotten; TC_ERR_NOT_FOUND for unknown tickets. */
 TC_API int tc_serve_poll(tc_server* s, uint64_t ticket, int* done, uint64_t* count, int* status);
+/* Stop accepting, cancel queued requests, finish the ones running, join the
+ * threads and free the resident graphs.  NULL is a no-op. */
 TC_API int tc_serve_destroy(tc_server* s);
 
 #ifdef __cplusplus

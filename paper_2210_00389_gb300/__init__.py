@@ -328,8 +328,11 @@ def tc_count_batch(graphs, mode: int = TC_MODE_COVER, opt: Options | None = None
 
 
 def tc_serve_create(hbm_budget_bytes: int, slots: int = 64, queue_capacity: int = 4096,
-                    wait_limit_ms: int = 0) -> int:
-    cfg = ServeConfig(hbm_budget_bytes, slots, queue_capacity, wait_limit_ms)
+                    wait_limit_ms: int = 0, fail_request: int = 0) -> int:
+    """``fail_request`` = k > 0 injects a host-side allocation failure into the
+    k-th admitted request (tests of failure handling)."""
+    res = (ctypes.c_int32 * 4)(fail_request, 0, 0, 0)
+    cfg = ServeConfig(hbm_budget_bytes, slots, queue_capacity, wait_limit_ms, res)
     h = _vp()
     _check(_lib.tc_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "tc_serve_create")
     return h.value

@@ -50,7 +50,11 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "rmat10", "rmat18", "rmat20", "chunglu23", "batch"])
+                    choices=["rmat22", "rmat10", "rmat18", "rmat20", "chunglu23", "batch",
+                             "serve"])
+    ap.add_argument("--requests", type=int, default=20000, help="serve: stream length")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
+    ap.add_argument("--serve-scale", type=int, default=26, help="serve: resident R-MAT scale")
     ap.add_argument("--arm", default="all", choices=["all", "cover", "plain"],
                     help="'cover' or 'plain' runs only that device-resident arm "
                          "(for profiling one step); 'all' is the benchmark")
@@ -504,10 +508,148 @@ def run_batch(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, world, rank, local):
+    """Serving: a resident R-MAT scale 26 graph (relabel seed 5) and an
+    open-loop Poisson stream of requests (seed 11) drawn like the mixed
+    batch with 5% R-MAT scale 18-22; latency = scheduled arrival -> poll sees
+    the result.  Compared with one-at-a-time FIFO plain counting of the same
+    stream.  Request graphs come from a seeded pool (every distinct small
+    spec of the first 2,000, and 2 graphs per large scale), generated before
+    timing."""
+    import random
+    import threading
+
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_2210_00389_gb300 as tc
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nreq, rate = args.requests, args.rate
+    rng = random.Random(11)
+    big = gg.rmat(args.serve_scale, 16, 5, relabel_seed=5 + 2**32)
+    small_specs = gg.mixed_graph_specs(2000, seed=11)
+    pool_small = [gg.graph_from_spec(s) for s in small_specs]
+    pool_large = [gg.rmat(sc, 16, 1000 + 10 * sc + k, relabel_seed=2000 + 10 * sc + k)
+                  for sc in range(18, 23) for k in range(2)]
+    # request mix: request 0 is the resident graph; then 5% large, the rest
+    # drawn from the small pool (which already has the 84/10/1 mix)
+    reqs = [("resident", None)]
+    for _ in range(nreq - 1):
+        if rng.random() < 0.05:
+            reqs.append(("large", rng.randrange(len(pool_large))))
+        else:
+            reqs.append(("small", rng.randrange(len(pool_small))))
+    t_arr = np.cumsum([0.0] + [rng.expovariate(rate) for _ in range(nreq - 1)])
+
+    def graph_of(kind, i):
+        return big if kind == "resident" else (pool_large[i] if kind == "large" else pool_small[i])
+
+    # expected counts: every distinct graph counted alone
+    alone = {}
+    for kind, pool in (("small", pool_small), ("large", pool_large)):
+        for i, g in enumerate(pool):
+            with tc.Graph(g.offsets, g.cols) as G:
+                alone[(kind, i)] = G.count(tc.TC_MODE_COVER)
+    units = [graph_of(k, i).num_edges for k, i in reqs]
+
+    # ---- served, continuous batching
+    s = tc.tc_serve_create(150 << 30, slots=64, queue_capacity=1 << 16, wait_limit_ms=600000)
+    gid = tc.tc_serve_register(s, big.offsets, big.cols)
+    done_at = [None] * nreq
+    result = [None] * nreq
+    tickets = [None] * nreq
+    lock = threading.Lock()
+    finished = threading.Event()
+
+    def poller():
+        pending = set()
+        while True:
+            with lock:
+                pending |= {i for i in range(nreq) if tickets[i] is not None and done_at[i] is None}
+            for i in list(pending):
+                d, c, st = tc.tc_serve_poll(s, tickets[i])
+                if d:
+                    done_at[i] = time.perf_counter()
+                    result[i] = (c, st)
+                    pending.discard(i)
+            if all(x is not None for x in done_at):
+                finished.set()
+                return
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=poller, daemon=True)
+    t0 = time.perf_counter()
+    th.start()
+    for i, (kind, j) in enumerate(reqs):
+        wait = t0 + t_arr[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        if kind == "resident":
+            t = tc.tc_serve_submit(s, None, gid, tc.TC_MODE_COVER)
+        else:
+            g = graph_of(kind, j)
+            t = tc.tc_serve_submit(s, (g.offsets, g.cols), 0, tc.TC_MODE_COVER)
+        with lock:
+            tickets[i] = t
+    finished.wait(timeout=1800)
+    t_end = time.perf_counter()
+    tc.tc_serve_destroy(s)
+    lat = np.array([done_at[i] - (t0 + t_arr[i]) for i in range(nreq)]) * 1e3
+    resident_T = result[0][0]
+    ok = all(result[i][1] == tc.TC_OK for i in range(nreq))
+    same = all(result[i][0] == (resident_T if reqs[i][0] == "resident" else alone[reqs[i]])
+               for i in range(nreq))
+
+    # ---- baseline: one at a time, FIFO, plain count
+    base_done = [0.0] * nreq
+    with tc.Graph(torch.from_numpy(big.offsets).to(dev), torch.from_numpy(big.cols).to(dev)) as B:
+        b0 = time.perf_counter()
+        for i, (kind, j) in enumerate(reqs):
+            wait = b0 + t_arr[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            if kind == "resident":
+                c = B.count(tc.TC_MODE_PLAIN)
+            else:
+                g = graph_of(kind, j)
+                with tc.Graph(g.offsets, g.cols) as G:
+                    c = G.count(tc.TC_MODE_PLAIN)
+            assert c == (resident_T if kind == "resident" else alone[(kind, j)])
+            base_done[i] = time.perf_counter()
+        b_end = time.perf_counter()
+    blat = np.array([base_done[i] - (b0 + t_arr[i]) for i in range(nreq)]) * 1e3
+
+    def pct(a, q):
+        return float(np.percentile(a, q))
+
+    line = {
+        "metric": METRIC, "value": sum(units) / (t_end - t0), "unit": "edges/s",
+        "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": (t_end - t0) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"serving: resident R-MAT scale {args.serve_scale} + Poisson "
+                               f"stream of {nreq} requests at {rate:g} req/s (seed 11)",
+                   "requests": nreq, "offered_req_per_s": rate,
+                   "resident_edges": big.num_edges, "resident_triangles": resident_T},
+        "serve": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": float(lat.max()),
+                  "achieved_req_per_s": nreq / (t_end - t0), "all_ok": ok,
+                  "each_equals_alone": same},
+        "fifo_plain": {"p50_ms": pct(blat, 50), "p99_ms": pct(blat, 99),
+                       "achieved_req_per_s": nreq / (b_end - b0),
+                       "value": sum(units) / (b_end - b0)},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_init()
-    if args.workload == "batch" and args.impl == "ours":
+    if args.workload == "serve" and args.impl == "ours":
+        run_serve(args, world, rank, local)
+    elif args.workload == "batch" and args.impl == "ours":
         run_batch(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)

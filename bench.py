@@ -563,21 +563,26 @@ def run_serve(args, world, rank, local):
     lock = threading.Lock()
     finished = threading.Event()
 
+    new_items = []  # submitted indices not yet seen by the poller
+
     def poller():
-        pending = set()
-        while True:
+        pending, ndone = [], 0
+        while ndone < nreq:
             with lock:
-                pending |= {i for i in range(nreq) if tickets[i] is not None and done_at[i] is None}
-            for i in list(pending):
+                pending.extend(new_items)
+                new_items.clear()
+            still = []
+            for i in pending:
                 d, c, st = tc.tc_serve_poll(s, tickets[i])
                 if d:
                     done_at[i] = time.perf_counter()
                     result[i] = (c, st)
-                    pending.discard(i)
-            if all(x is not None for x in done_at):
-                finished.set()
-                return
-            time.sleep(0.0005)
+                    ndone += 1
+                else:
+                    still.append(i)
+            pending = still
+            time.sleep(0.0002)
+        finished.set()
 
     th = threading.Thread(target=poller, daemon=True)
     t0 = time.perf_counter()
@@ -593,6 +598,7 @@ def run_serve(args, world, rank, local):
             t = tc.tc_serve_submit(s, (g.offsets, g.cols), 0, tc.TC_MODE_COVER)
         with lock:
             tickets[i] = t
+            new_items.append(i)
     finished.wait(timeout=1800)
     t_end = time.perf_counter()
     tc.tc_serve_destroy(s)

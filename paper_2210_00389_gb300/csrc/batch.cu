@@ -223,6 +223,34 @@ static void launch_batch(int grid, cudaStream_t s, const BGraph* graphs, const u
          counts, status, queue);
 }
 
+// Grow-only pinned staging buffer, one per host thread, kept until the
+// thread exits: freeing pinned memory (cudaFreeHost) synchronises the whole
+// device, which would serialise concurrent callers such as the server's
+// workers.
+struct PinnedStaging {
+  unsigned char* p = nullptr;
+  size_t n = 0;
+  ~PinnedStaging() {
+    if (p) cudaFreeHost(p);
+  }
+};
+
+static unsigned char* pinned_staging(size_t bytes) {
+  static thread_local PinnedStaging st;
+  if (st.n >= bytes) return st.p;
+  const size_t want = std::max(bytes, st.n * 2);
+  if (st.p) cudaFreeHost(st.p);
+  st.p = nullptr;
+  st.n = 0;
+  if (cudaMallocHost(reinterpret_cast<void**>(&st.p), want) != cudaSuccess) {
+    cudaGetLastError();
+    st.p = nullptr;
+    return nullptr;
+  }
+  st.n = want;
+  return st.p;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -284,8 +312,7 @@ extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mo
     do {
       std::vector<BGraph> hg(small.size());
       if (host_bytes > 0) {
-        if (cudaMallocHost(&pinned, host_bytes) != cudaSuccess) {
-          cudaGetLastError();
+        if (!(pinned = pinned_staging(host_bytes))) {
           rc = fail(TC_ERR_OOM, "tc_count_batch: pinned staging of %zu bytes failed", host_bytes);
           break;
         }
@@ -357,14 +384,16 @@ extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mo
       if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) == cudaSuccess &&
           (e = cudaEventRecord(done, cs)) == cudaSuccess &&
           (e = cudaStreamWaitEvent(user, done, 0)) == cudaSuccess &&
-          (e = cudaGraphLaunch(exec, user)) == cudaSuccess &&
-          (e = cudaStreamSynchronize(user)) == cudaSuccess) {
+          (e = cudaGraphLaunch(exec, user)) == cudaSuccess) {
         std::vector<unsigned long long> c(hg.size());
         std::vector<int> s(hg.size());
-        e = cudaMemcpy(c.data(), dcounts.p, sizeof(unsigned long long) * c.size(),
-                       cudaMemcpyDeviceToHost);
+        // read-back on the caller's stream (no legacy-stream synchronisation)
+        e = cudaMemcpyAsync(c.data(), dcounts.p, sizeof(unsigned long long) * c.size(),
+                            cudaMemcpyDeviceToHost, user);
         if (e == cudaSuccess)
-          e = cudaMemcpy(s.data(), dstatus.p, sizeof(int) * s.size(), cudaMemcpyDeviceToHost);
+          e = cudaMemcpyAsync(s.data(), dstatus.p, sizeof(int) * s.size(),
+                              cudaMemcpyDeviceToHost, user);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(user);
         if (e == cudaSuccess) {
           for (size_t k = 0; k < small.size(); ++k) {
             cnt_host[small[k]] = c[k];
@@ -387,7 +416,6 @@ extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mo
     dstatus.release();
     cudaStreamSynchronize(cs);
     cudaStreamDestroy(cs);
-    if (pinned) cudaFreeHost(pinned);
     if (rc != TC_OK) return rc;
   }
   // graphs too large for one CTA: the single-graph path

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstring>
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -299,11 +300,20 @@ int tc_serve_submit(tc_server* s, const tc_csr_view* csr_or_null, uint64_t graph
     // as soon as this returns
     r->off.resize((size_t)v.n + 1);
     r->cols.resize((size_t)v.nnz);
-    TC_CUDA(cudaMemcpy(r->off.data(), v.offsets, sizeof(int64_t) * r->off.size(),
-                       cudaMemcpyDefault));
-    if (v.nnz > 0)
-      TC_CUDA(cudaMemcpy(r->cols.data(), v.cols, sizeof(uint32_t) * r->cols.size(),
-                         cudaMemcpyDefault));
+    if (is_device_ptr(v.offsets)) {
+      TC_CUDA(cudaMemcpy(r->off.data(), v.offsets, sizeof(int64_t) * r->off.size(),
+                         cudaMemcpyDeviceToHost));
+    } else {
+      memcpy(r->off.data(), v.offsets, sizeof(int64_t) * r->off.size());
+    }
+    if (v.nnz > 0) {
+      if (is_device_ptr(v.cols)) {
+        TC_CUDA(cudaMemcpy(r->cols.data(), v.cols, sizeof(uint32_t) * r->cols.size(),
+                           cudaMemcpyDeviceToHost));
+      } else {
+        memcpy(r->cols.data(), v.cols, sizeof(uint32_t) * r->cols.size());
+      }
+    }
     r->n = v.n;
     r->small = v.n <= kServeSmallN && v.nnz <= kServeSmallNnz;
     r->est_bytes = r->small ? 2 * csr_bytes(v.n, v.nnz) + (size_t)v.n * 16

@@ -34,6 +34,29 @@ static tc_alloc_fn g_alloc = nullptr;
 static tc_free_fn g_free = nullptr;
 static void* g_alloc_ctx = nullptr;
 
+// The device's default stream-ordered memory pool returns freed memory to
+// the system at every synchronisation unless told otherwise; remapping it
+// on the next allocation costs milliseconds and serialises concurrent work.
+// Once per device (per process), let the pool keep what it has.
+static void keep_pool_memory() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  done[dev] = true;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+}
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t stream) {
   *p = nullptr;
   if (bytes == 0) bytes = 1;
@@ -49,6 +72,7 @@ int dev_alloc(void** p, size_t bytes, cudaStream_t stream) {
     if (!*p) return fail(TC_ERR_OOM, "allocator hook returned NULL for %zu bytes", bytes);
     return TC_OK;
   }
+  keep_pool_memory();
   cudaError_t e = cudaMallocAsync(p, bytes, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();

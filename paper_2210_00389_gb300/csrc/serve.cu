@@ -15,9 +15,14 @@
 //    admitted in time finishes with TC_ERR_TIMEOUT instead of waiting forever.
 //  * Host-side fault injection for tests: reserved[0] = k > 0 makes the k-th
 //    admitted request fail with TC_ERR_OOM as if its allocation had failed.
+//  * Tracing: with TC_SERVE_TRACE=<path> in the environment the server writes
+//    one line per device job (kind B/L/R = batch / large / resident, start
+//    and end seconds since creation, requests in the job) when destroyed.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <condition_variable>
 #include <deque>
@@ -95,6 +100,17 @@ struct tc_server {
   uint64_t next_ticket = 1;
   uint64_t next_graph = 1;
   uint64_t admitted = 0;
+  // optional trace (TC_SERVE_TRACE=<path>): one record per device job
+  struct TraceRec { char kind; double t0, t1; size_t nreq; };
+  std::vector<TraceRec> trace;
+  Clock::time_point t_create = Clock::now();
+  bool tracing = false;
+  void record(char kind, Clock::time_point a, Clock::time_point b, size_t nreq) {
+    if (!tracing) return;
+    std::lock_guard<std::mutex> lk(mu);
+    trace.push_back({kind, std::chrono::duration<double>(a - t_create).count(),
+                     std::chrono::duration<double>(b - t_create).count(), nreq});
+  }
   bool stopping = false;
   std::thread scheduler;
   std::vector<std::thread> workers;
@@ -168,6 +184,7 @@ struct tc_server {
       }
       uint64_t c = 0;
       int st = TC_OK;
+      const auto ta = Clock::now();
       if (r->graph_id) {
         Resident* res = nullptr;
         {
@@ -190,6 +207,7 @@ struct tc_server {
         std::vector<int64_t>().swap(r->off);
         std::vector<uint32_t>().swap(r->cols);
       }
+      record(r->graph_id ? 'R' : 'L', ta, Clock::now(), 1);
       finish(r, st, st == TC_OK ? c : 0);
     }
     cudaStreamSynchronize(s);
@@ -219,6 +237,7 @@ struct tc_server {
         }
       }
       if (group.empty()) continue;
+      const auto ta = Clock::now();
       std::vector<tc_csr_view> views(group.size());
       for (size_t i = 0; i < group.size(); ++i)
         views[i] = tc_csr_view{group[i]->off.data(), group[i]->cols.data(), group[i]->n,
@@ -227,6 +246,7 @@ struct tc_server {
       std::vector<int> status(group.size(), TC_OK);
       const int rc = tc_count_batch(views.data(), (int32_t)views.size(), group[0]->mode, nullptr,
                                     s, counts.data(), status.data());
+      record('B', ta, Clock::now(), group.size());
       for (size_t i = 0; i < group.size(); ++i) {
         std::vector<int64_t>().swap(group[i]->off);
         std::vector<uint32_t>().swap(group[i]->cols);
@@ -249,6 +269,7 @@ int tc_serve_create(const tc_serve_config* cfg, tc_server** out) {
   s->cfg = *cfg;
   if (s->cfg.queue_capacity <= 0) s->cfg.queue_capacity = 4096;
   cudaGetDevice(&s->device);
+  s->tracing = getenv("TC_SERVE_TRACE") != nullptr;
   s->scheduler = std::thread([s] { s->schedule_loop(); });
   for (int i = 0; i < kLargeWorkers; ++i) s->workers.emplace_back([s] { s->large_worker(); });
   s->workers.emplace_back([s] { s->batch_worker(); });
@@ -380,6 +401,12 @@ int tc_serve_destroy(tc_server* s) {
   if (s->scheduler.joinable()) s->scheduler.join();
   for (auto& t : s->workers)
     if (t.joinable()) t.join();
+  if (s->tracing) {
+    if (FILE* f = fopen(getenv("TC_SERVE_TRACE"), "w")) {
+      for (const auto& r : s->trace) fprintf(f, "%c %.6f %.6f %zu\n", r.kind, r.t0, r.t1, r.nreq);
+      fclose(f);
+    }
+  }
   for (auto& kv : s->residents) {
     tc_graph_destroy(kv.second->g);
     cudaStreamDestroy(kv.second->stream);

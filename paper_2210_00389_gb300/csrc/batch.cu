@@ -18,8 +18,8 @@
 //   reduce   warp shuffles, then one 64-bit store per graph.
 // There is no host synchronisation per BFS level or per graph.  The launch
 // is captured into a CUDA graph on an internal stream and replayed on the
-// caller's stream.  Graphs with more than kBatchMaxN vertices take the
-// single-graph path instead.
+// caller's stream.  Graphs with more than kBatchMaxN vertices or
+// kBatchMaxNnz entries go to the union path below instead.
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -29,7 +29,8 @@
 
 namespace tc {
 
-constexpr uint32_t kBatchMaxN = 1u << 16;  // vertices per graph in the batch kernel
+constexpr uint32_t kBatchMaxN = 1u << 16;     // vertices per graph in the batch kernel
+constexpr int64_t kBatchMaxNnz = 1ll << 15;   // entries per graph in the batch kernel
 
 struct BGraph {
   const int64_t* off;
@@ -251,6 +252,291 @@ static unsigned char* pinned_staging(size_t bytes) {
   return st.p;
 }
 
+
+// ---------------------------------------------------------------- union path
+// Members too large for one CTA are counted together: they are packed into
+// one disjoint-union graph (vertex ids and entry positions shifted), counted
+// once by the single-graph pipeline (levels, segmented rows, bucketing, hash
+// intersection) with per-edge counts, and each member's count is the sum of
+// its own contiguous range of per-edge counts.  Counts do not depend on the
+// BFS roots (Thm. 2 holds for any BFS), so the union's roots give every
+// member its exact count.
+
+// Block per member: the same CSR checks as the batch kernel.
+__global__ void k_member_check(const BGraph* __restrict__ graphs, int32_t nm, int* __restrict__ st) {
+  for (int32_t m = blockIdx.x; m < nm; m += gridDim.x) {
+    const BGraph G = graphs[m];
+    bool bad = false;
+    for (uint32_t v = threadIdx.x; v <= G.n; v += blockDim.x) {
+      const int64_t o = G.off[v];
+      if (o < 0 || o > G.nnz || (v == 0 && o != 0) || (v == G.n && o != G.nnz)) bad = true;
+      else if (v < G.n && G.off[v + 1] < o) bad = true;
+    }
+    if (__syncthreads_or(bad)) {
+      if (threadIdx.x == 0) st[m] = TC_ERR_INVALID_GRAPH;
+      continue;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t v = wid; v < G.n; v += nw) {
+      const int64_t b = G.off[v], e = G.off[v + 1];
+      for (int64_t i = b + lane; i < e; i += 32) {
+        const uint32_t w = G.cols[i];
+        if (w >= G.n || w == v || (i > b && G.cols[i - 1] >= w)) bad = true;
+      }
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) st[m] = bad ? TC_ERR_INVALID_GRAPH : TC_OK;
+  }
+}
+
+// Block per packed member: shifted offsets and column ids.
+__global__ void k_member_pack(const BGraph* __restrict__ graphs, const uint32_t* __restrict__ mem,
+                              const unsigned long long* __restrict__ vbase,
+                              const unsigned long long* __restrict__ ebase, int32_t np,
+                              int64_t* __restrict__ uoff, uint32_t* __restrict__ ucols) {
+  for (int32_t k = blockIdx.x; k < np; k += gridDim.x) {
+    const BGraph G = graphs[mem[k]];
+    const unsigned long long vb = vbase[k], eb = ebase[k];
+    for (uint32_t v = threadIdx.x; v < G.n; v += blockDim.x) uoff[vb + v] = (int64_t)eb + G.off[v];
+    for (int64_t i = threadIdx.x; i < G.nnz; i += blockDim.x)
+      ucols[eb + i] = (uint32_t)vb + G.cols[i];
+  }
+}
+
+// Block per packed member: sum of its per-edge counts.  Cover edges of a
+// member are H[hoff[vb] .. hoff[vb + n]) (H is in vertex order); plain
+// entries are [eb, eb + nnz).
+__global__ void k_member_sums(const BGraph* __restrict__ graphs, const uint32_t* __restrict__ mem,
+                              const unsigned long long* __restrict__ vbase,
+                              const unsigned long long* __restrict__ ebase, int32_t np, int mode,
+                              const unsigned long long* __restrict__ hoff, uint64_t total_n,
+                              uint64_t num_cover, const uint32_t* __restrict__ per_edge,
+                              unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long red[32];
+  for (int32_t k = blockIdx.x; k < np; k += gridDim.x) {
+    const BGraph G = graphs[mem[k]];
+    unsigned long long a, b;
+    if (mode == TC_MODE_COVER) {
+      const unsigned long long ve = vbase[k] + G.n;
+      a = hoff[vbase[k]];
+      b = ve < total_n ? hoff[ve] : num_cover;
+    } else {
+      a = ebase[k];
+      b = ebase[k] + (unsigned long long)G.nnz;
+    }
+    unsigned long long s = 0;
+    for (unsigned long long i = a + threadIdx.x; i < b; i += blockDim.x) s += per_edge[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      out[k] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Device descriptors for graphs[idx[...]]: device views are used in place,
+// host views are staged through pinned memory into one device arena.
+static int make_descs(const tc_csr_view* graphs, const std::vector<int32_t>& idx, cudaStream_t cs,
+                      std::vector<BGraph>& hg, DevBuf<unsigned char>& arena) {
+  size_t host_bytes = 0;
+  for (int32_t i : idx) {
+    const tc_csr_view& v = graphs[i];
+    if (!(v.on_device && is_device_ptr(v.offsets))) {
+      host_bytes += (sizeof(int64_t) * ((size_t)v.n + 1) + 15) & ~(size_t)15;
+      host_bytes += (sizeof(uint32_t) * (size_t)v.nnz + 15) & ~(size_t)15;
+    }
+  }
+  unsigned char* pinned = nullptr;
+  if (host_bytes > 0) {
+    if (!(pinned = pinned_staging(host_bytes)))
+      return fail(TC_ERR_OOM, "tc_count_batch: pinned staging of %zu bytes failed", host_bytes);
+    TC_TRY(arena.alloc(host_bytes, cs));
+  }
+  hg.resize(idx.size());
+  size_t pos = 0;
+  for (size_t k = 0; k < idx.size(); ++k) {
+    const tc_csr_view& v = graphs[idx[k]];
+    BGraph b{};
+    b.n = v.n;
+    b.nnz = v.nnz;
+    if (v.on_device && is_device_ptr(v.offsets)) {
+      b.off = v.offsets;
+      b.cols = v.cols;
+    } else {
+      const size_t ob = sizeof(int64_t) * ((size_t)v.n + 1);
+      memcpy(pinned + pos, v.offsets, ob);
+      b.off = reinterpret_cast<const int64_t*>(arena.p + pos);
+      pos = (pos + ob + 15) & ~(size_t)15;
+      const size_t cb = sizeof(uint32_t) * (size_t)v.nnz;
+      if (cb) memcpy(pinned + pos, v.cols, cb);
+      b.cols = reinterpret_cast<const uint32_t*>(arena.p + pos);
+      pos = (pos + cb + 15) & ~(size_t)15;
+    }
+    hg[k] = b;
+  }
+  if (host_bytes > 0)
+    TC_CUDA(cudaMemcpyAsync(arena.p, pinned, host_bytes, cudaMemcpyHostToDevice, cs));
+  // the staging buffer is reused by the next call on this thread
+  TC_CUDA(cudaStreamSynchronize(cs));
+  return TC_OK;
+}
+
+// Tiny members: one persistent launch, captured into a CUDA graph on `cs`
+// and replayed on `user`.
+static int run_tiny(const tc_csr_view* graphs, const std::vector<int32_t>& idx, int mode,
+                    int threads, int per_sm, int64_t skew, cudaStream_t cs, cudaStream_t user,
+                    std::vector<unsigned long long>& cnt, std::vector<int>& st) {
+  std::vector<BGraph> hg;
+  DevBuf<unsigned char> arena;
+  TC_TRY(make_descs(graphs, idx, cs, hg, arena));
+  uint32_t max_n = 1;
+  for (const BGraph& b : hg) max_n = std::max(max_n, b.n + 1);
+  std::vector<uint32_t> ord(hg.size());  // largest graphs first
+  std::iota(ord.begin(), ord.end(), 0u);
+  std::stable_sort(ord.begin(), ord.end(),
+                   [&](uint32_t a, uint32_t b) { return hg[a].nnz > hg[b].nnz; });
+  const int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, (int64_t)hg.size());
+  DevBuf<BGraph> dgraphs;
+  DevBuf<uint32_t> dorder, scratch;
+  DevBuf<unsigned long long> dcounts, dqueue;
+  DevBuf<int> dstatus;
+  TC_TRY(dgraphs.alloc(hg.size(), cs));
+  TC_TRY(dorder.alloc(ord.size(), cs));
+  TC_TRY(dcounts.alloc(hg.size(), cs));
+  TC_TRY(dstatus.alloc(hg.size(), cs));
+  TC_TRY(dqueue.alloc(1, cs));
+  TC_TRY(scratch.alloc((size_t)grid * 4 * max_n, cs));
+  TC_CUDA(cudaMemcpyAsync(dgraphs.p, hg.data(), sizeof(BGraph) * hg.size(), cudaMemcpyHostToDevice,
+                          cs));
+  TC_CUDA(cudaMemcpyAsync(dorder.p, ord.data(), sizeof(uint32_t) * ord.size(),
+                          cudaMemcpyHostToDevice, cs));
+  TC_CUDA(cudaStreamSynchronize(cs));
+  cudaGraph_t cg = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  TC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(dqueue.p, 0, sizeof(unsigned long long), cs);
+  const int32_t ng = (int32_t)hg.size();
+  if (threads == 128)
+    launch_batch<128>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
+                      dstatus.p, dqueue.p);
+  else if (threads == 256)
+    launch_batch<256>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
+                      dstatus.p, dqueue.p);
+  else
+    launch_batch<512>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
+                      dstatus.p, dqueue.p);
+  TC_CUDA(cudaStreamEndCapture(cs, &cg));
+  cudaError_t e = cudaGraphInstantiate(&exec, cg, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, user);
+  std::vector<unsigned long long> c(hg.size());
+  std::vector<int> s(hg.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c.data(), dcounts.p, sizeof(unsigned long long) * c.size(),
+                        cudaMemcpyDeviceToHost, user);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s.data(), dstatus.p, sizeof(int) * s.size(), cudaMemcpyDeviceToHost, user);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(user);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (cg) cudaGraphDestroy(cg);
+  if (e != cudaSuccess) return cuda_fail(e, "batched launch", __FILE__, __LINE__);
+  for (size_t k = 0; k < idx.size(); ++k) {
+    cnt[idx[k]] = c[k];
+    st[idx[k]] = s[k];
+  }
+  return TC_OK;
+}
+
+static int run_union(const tc_csr_view* graphs, const std::vector<int32_t>& idx, int mode,
+                     cudaStream_t cs, std::vector<unsigned long long>& cnt, std::vector<int>& st) {
+  std::vector<BGraph> hg;
+  DevBuf<unsigned char> arena;
+  TC_TRY(make_descs(graphs, idx, cs, hg, arena));
+  const int32_t nm = (int32_t)hg.size();
+  DevBuf<BGraph> dgraphs;
+  DevBuf<int> dst;
+  TC_TRY(dgraphs.alloc(hg.size(), cs));
+  TC_TRY(dst.alloc(hg.size(), cs));
+  TC_CUDA(cudaMemcpyAsync(dgraphs.p, hg.data(), sizeof(BGraph) * hg.size(), cudaMemcpyHostToDevice,
+                          cs));
+  launch(k_member_check, std::min(nm, sm_count() * 8), 256, 0, cs, dgraphs.p, nm, dst.p);
+  std::vector<int> mst(hg.size());
+  TC_CUDA(cudaMemcpyAsync(mst.data(), dst.p, sizeof(int) * mst.size(), cudaMemcpyDeviceToHost, cs));
+  TC_CUDA(cudaStreamSynchronize(cs));
+  // valid members and their vertex / entry bases in the union
+  std::vector<uint32_t> mem;
+  std::vector<unsigned long long> vb, eb;
+  unsigned long long tn = 0, te = 0;
+  for (int32_t k = 0; k < nm; ++k) {
+    st[idx[k]] = mst[k];
+    cnt[idx[k]] = 0;
+    if (mst[k] != TC_OK) continue;
+    mem.push_back((uint32_t)k);
+    vb.push_back(tn);
+    eb.push_back(te);
+    tn += hg[k].n;
+    te += (unsigned long long)hg[k].nnz;
+  }
+  if (mem.empty()) return TC_OK;
+  if (tn >= 0xFFFFFFFFull || te >= 0xFFFFFFFFull)
+    return fail(TC_ERR_CAPACITY, "tc_count_batch: union of large graphs exceeds 2^32 ids/entries");
+  const int32_t np = (int32_t)mem.size();
+  DevBuf<uint32_t> dmem, ucols;
+  DevBuf<unsigned long long> dvb, deb, dout;
+  DevBuf<int64_t> uoff;
+  TC_TRY(dmem.alloc(mem.size(), cs));
+  TC_TRY(dvb.alloc(vb.size(), cs));
+  TC_TRY(deb.alloc(eb.size(), cs));
+  TC_TRY(dout.alloc(mem.size(), cs));
+  TC_TRY(uoff.alloc((size_t)tn + 1, cs));
+  TC_TRY(ucols.alloc((size_t)te, cs));
+  TC_CUDA(cudaMemcpyAsync(dmem.p, mem.data(), sizeof(uint32_t) * mem.size(), cudaMemcpyHostToDevice,
+                          cs));
+  TC_CUDA(cudaMemcpyAsync(dvb.p, vb.data(), sizeof(unsigned long long) * vb.size(),
+                          cudaMemcpyHostToDevice, cs));
+  TC_CUDA(cudaMemcpyAsync(deb.p, eb.data(), sizeof(unsigned long long) * eb.size(),
+                          cudaMemcpyHostToDevice, cs));
+  const int64_t last = (int64_t)te;
+  TC_CUDA(cudaMemcpyAsync(uoff.p + tn, &last, sizeof(int64_t), cudaMemcpyHostToDevice, cs));
+  launch(k_member_pack, std::min(np, sm_count() * 8), 256, 0, cs, dgraphs.p, dmem.p, dvb.p, deb.p,
+         np, uoff.p, ucols.p);
+  TC_CUDA(cudaGetLastError());
+  TC_CUDA(cudaStreamSynchronize(cs));  // `last` lives on this stack frame
+  tc_csr_view uv{uoff.p, ucols.p, (uint32_t)tn, (int64_t)te, 1};
+  tc_graph* g = nullptr;
+  TC_TRY(tc_graph_create(&uv, TC_GRAPH_BORROW, cs, &g));
+  int rc = TC_OK;
+  DevBuf<uint32_t> per_edge;
+  uint64_t total = 0;
+  if (mode == TC_MODE_COVER) {
+    rc = compute_cover(g);
+    if (rc == TC_OK) rc = per_edge.alloc((size_t)std::max<int64_t>(g->num_cover, 1), cs);
+    if (rc == TC_OK) rc = count_cover(g, per_edge.p, &total);
+  } else {
+    rc = per_edge.alloc((size_t)te, cs);
+    if (rc == TC_OK) rc = count_plain(g, &total, per_edge.p);
+  }
+  if (rc == TC_OK) {
+    launch(k_member_sums, std::min(np, sm_count() * 8), 256, 0, cs, dgraphs.p, dmem.p, dvb.p,
+           deb.p, np, mode, g->hoff.p, (uint64_t)tn, (uint64_t)std::max<int64_t>(g->num_cover, 0),
+           per_edge.p, dout.p);
+    std::vector<unsigned long long> out(mem.size());
+    cudaError_t e = cudaMemcpyAsync(out.data(), dout.p, sizeof(unsigned long long) * out.size(),
+                                    cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "union sums", __FILE__, __LINE__);
+    } else {
+      for (size_t k = 0; k < mem.size(); ++k) cnt[idx[mem[k]]] = out[k];
+    }
+  }
+  tc_graph_destroy(g);
+  return rc;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -263,175 +549,33 @@ extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mo
   if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
     return fail(TC_ERR_INVALID_ARG, "tc_count_batch: unknown mode %d", mode);
   if (ngraphs == 0) return TC_OK;
-  int threads = opt && opt->block_threads > 0 ? opt->block_threads : 256;
+  const int threads = opt && opt->block_threads > 0 ? opt->block_threads : 256;
   int per_sm = opt && opt->blocks_per_sm > 0 ? opt->blocks_per_sm : 4;
   if (threads != 128 && threads != 256 && threads != 512)
     return fail(TC_ERR_INVALID_ARG, "tc_count_batch: block_threads must be 128, 256 or 512");
   if (per_sm > 16) per_sm = 16;
   const int64_t skew = opt && opt->skew >= 2 ? opt->skew : kSkew;
-  cudaStream_t user = (cudaStream_t)cuda_stream;
-
-  // split: graphs the batch kernel takes, and large ones for the single-graph path
-  std::vector<int32_t> small, large;
+  std::vector<int32_t> tiny, rest;
   for (int32_t i = 0; i < ngraphs; ++i) {
     const tc_csr_view& v = graphs[i];
     if (!v.offsets || v.nnz < 0 || (v.nnz > 0 && !v.cols))
       return fail(TC_ERR_INVALID_ARG, "tc_count_batch: graph %d has NULL arrays or nnz < 0", i);
-    (v.n <= kBatchMaxN ? small : large).push_back(i);
+    (v.n <= kBatchMaxN && v.nnz <= kBatchMaxNnz ? tiny : rest).push_back(i);
   }
-  std::vector<int> st_host((size_t)ngraphs, TC_OK);
-  std::vector<unsigned long long> cnt_host((size_t)ngraphs, 0ull);
-
-  if (!small.empty()) {
-    // descriptors: device views are used in place; host views are packed
-    // into one pinned arena and copied with a single transfer
-    size_t host_bytes = 0;
-    uint32_t max_n = 1;
-    for (int32_t i : small) {
-      const tc_csr_view& v = graphs[i];
-      max_n = std::max(max_n, v.n + 1);
-      if (!(v.on_device && is_device_ptr(v.offsets))) {
-        host_bytes += sizeof(int64_t) * ((size_t)v.n + 1);
-        host_bytes = (host_bytes + 15) & ~(size_t)15;
-        host_bytes += sizeof(uint32_t) * (size_t)v.nnz;
-        host_bytes = (host_bytes + 15) & ~(size_t)15;
-      }
-    }
-    cudaStream_t cs = nullptr;
-    TC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    int rc = TC_OK;
-    unsigned char* pinned = nullptr;
-    DevBuf<unsigned char> arena;
-    DevBuf<BGraph> dgraphs;
-    DevBuf<uint32_t> dorder, scratch;
-    DevBuf<unsigned long long> dcounts, dqueue;
-    DevBuf<int> dstatus;
-    cudaGraph_t cg = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t done = nullptr;
-    do {
-      std::vector<BGraph> hg(small.size());
-      if (host_bytes > 0) {
-        if (!(pinned = pinned_staging(host_bytes))) {
-          rc = fail(TC_ERR_OOM, "tc_count_batch: pinned staging of %zu bytes failed", host_bytes);
-          break;
-        }
-        if ((rc = arena.alloc(host_bytes, cs)) != TC_OK) break;
-      }
-      size_t pos = 0;
-      for (size_t k = 0; k < small.size(); ++k) {
-        const tc_csr_view& v = graphs[small[k]];
-        BGraph b{};
-        b.n = v.n;
-        b.nnz = v.nnz;
-        if (v.on_device && is_device_ptr(v.offsets)) {
-          b.off = v.offsets;
-          b.cols = v.cols;
-        } else {
-          const size_t ob = sizeof(int64_t) * ((size_t)v.n + 1);
-          memcpy(pinned + pos, v.offsets, ob);
-          b.off = reinterpret_cast<const int64_t*>(arena.p + pos);
-          pos = (pos + ob + 15) & ~(size_t)15;
-          const size_t cb = sizeof(uint32_t) * (size_t)v.nnz;
-          if (cb) memcpy(pinned + pos, v.cols, cb);
-          b.cols = reinterpret_cast<const uint32_t*>(arena.p + pos);
-          pos = (pos + cb + 15) & ~(size_t)15;
-        }
-        hg[k] = b;
-      }
-      // largest graphs first
-      std::vector<uint32_t> ord(small.size());
-      std::iota(ord.begin(), ord.end(), 0u);
-      std::stable_sort(ord.begin(), ord.end(),
-                       [&](uint32_t a, uint32_t b) { return hg[a].nnz > hg[b].nnz; });
-      const int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, (int64_t)small.size());
-      if ((rc = dgraphs.alloc(hg.size(), cs)) != TC_OK) break;
-      if ((rc = dorder.alloc(ord.size(), cs)) != TC_OK) break;
-      if ((rc = dcounts.alloc(hg.size(), cs)) != TC_OK) break;
-      if ((rc = dstatus.alloc(hg.size(), cs)) != TC_OK) break;
-      if ((rc = dqueue.alloc(1, cs)) != TC_OK) break;
-      if ((rc = scratch.alloc((size_t)grid * 4 * max_n, cs)) != TC_OK) break;
-      cudaError_t e = cudaSuccess;
-      if (host_bytes > 0)
-        e = cudaMemcpyAsync(arena.p, pinned, host_bytes, cudaMemcpyHostToDevice, cs);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dgraphs.p, hg.data(), sizeof(BGraph) * hg.size(),
-                            cudaMemcpyHostToDevice, cs);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dorder.p, ord.data(), sizeof(uint32_t) * ord.size(),
-                            cudaMemcpyHostToDevice, cs);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "batch upload", __FILE__, __LINE__); break; }
-      // capture: reset the queue, one persistent launch
-      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__); break; }
-      cudaMemsetAsync(dqueue.p, 0, sizeof(unsigned long long), cs);
-      const int32_t ng = (int32_t)small.size();
-      if (threads == 128)
-        launch_batch<128>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
-                          dstatus.p, dqueue.p);
-      else if (threads == 256)
-        launch_batch<256>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
-                          dstatus.p, dqueue.p);
-      else
-        launch_batch<512>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
-                          dstatus.p, dqueue.p);
-      e = cudaStreamEndCapture(cs, &cg);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }
-      e = cudaGraphInstantiate(&exec, cg, 0);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); break; }
-      // replay on the caller's stream, ordered after the uploads
-      if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) == cudaSuccess &&
-          (e = cudaEventRecord(done, cs)) == cudaSuccess &&
-          (e = cudaStreamWaitEvent(user, done, 0)) == cudaSuccess &&
-          (e = cudaGraphLaunch(exec, user)) == cudaSuccess) {
-        std::vector<unsigned long long> c(hg.size());
-        std::vector<int> s(hg.size());
-        // read-back on the caller's stream (no legacy-stream synchronisation)
-        e = cudaMemcpyAsync(c.data(), dcounts.p, sizeof(unsigned long long) * c.size(),
-                            cudaMemcpyDeviceToHost, user);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(s.data(), dstatus.p, sizeof(int) * s.size(),
-                              cudaMemcpyDeviceToHost, user);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(user);
-        if (e == cudaSuccess) {
-          for (size_t k = 0; k < small.size(); ++k) {
-            cnt_host[small[k]] = c[k];
-            st_host[small[k]] = s[k];
-          }
-        }
-      }
-      if (e != cudaSuccess) { rc = cuda_fail(e, "batch launch", __FILE__, __LINE__); break; }
-    } while (0);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (cg) cudaGraphDestroy(cg);
-    if (done) cudaEventDestroy(done);
-    cudaStreamSynchronize(cs);
-    arena.release();
-    dgraphs.release();
-    dorder.release();
-    scratch.release();
-    dcounts.release();
-    dqueue.release();
-    dstatus.release();
-    cudaStreamSynchronize(cs);
-    cudaStreamDestroy(cs);
-    if (rc != TC_OK) return rc;
-  }
-  // graphs too large for one CTA: the single-graph path
-  for (int32_t i : large) {
-    tc_graph* g = nullptr;
-    int st = tc_graph_create(&graphs[i], TC_GRAPH_VALIDATE, cuda_stream, &g);
-    uint64_t c = 0;
-    if (st == TC_OK) st = tc_count(g, mode, &c);
-    tc_graph_destroy(g);
-    if (st != TC_OK && st != TC_ERR_INVALID_GRAPH) return st;
-    cnt_host[i] = st == TC_OK ? c : 0;
-    st_host[i] = st;
-  }
+  std::vector<int> st((size_t)ngraphs, TC_OK);
+  std::vector<unsigned long long> cnt((size_t)ngraphs, 0ull);
+  cudaStream_t user = (cudaStream_t)cuda_stream;
+  cudaStream_t cs = nullptr;
+  TC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int rc = TC_OK;
+  if (!tiny.empty()) rc = run_tiny(graphs, tiny, mode, threads, per_sm, skew, cs, user, cnt, st);
+  if (rc == TC_OK && !rest.empty()) rc = run_union(graphs, rest, mode, cs, cnt, st);
+  cudaStreamSynchronize(cs);
+  cudaStreamDestroy(cs);
+  if (rc != TC_OK) return rc;
   for (int32_t i = 0; i < ngraphs; ++i) {
-    counts_out[i] = cnt_host[i];
-    if (status_out) status_out[i] = st_host[i];
+    counts_out[i] = cnt[i];
+    if (status_out) status_out[i] = st[i];
   }
   return TC_OK;
 }

@@ -168,7 +168,7 @@ int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots);
 int compute_segments(tc_graph* g);
 int compute_cover(tc_graph* g);
 int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total);
-int count_plain(tc_graph* g, uint64_t* total);
+int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry = nullptr);
 
 // Exclusive scan of `n` 64-bit counts in place on `stream`; returns the
 // total through `total_dev` (device pointer, may be null).

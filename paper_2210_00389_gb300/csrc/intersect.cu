@@ -141,6 +141,10 @@ k_small_merge(int mode, const uint32_t* __restrict__ list, const unsigned long l
         const int64_t la = off[u + 1] - au, lb = off[v + 1] - bv;
         c = warp_intersect(cols + au, la, cols + bv, lb);
         if (lane == 0) elems += (unsigned long long)(la + lb);
+        if (per_edge) {
+          const unsigned long long t = warp_sum(c);
+          if (lane == 0) per_edge[i] = (uint32_t)t;
+        }
       }
       acc += c;
     }
@@ -251,21 +255,27 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
   return TC_OK;
 }
 
-int count_plain(tc_graph* g, uint64_t* total) {
+// per_entry (device, nnz entries, or NULL): the count of every CSR entry
+// (u, v) with u < v; other entries are left 0.
+int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry) {
   cudaStream_t s = g->stream;
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
   g->stats.ms_intersect = g->stats.ms_bucket = g->stats.ms_main_kernel = 0.f;
   const bool hashed = g->nnz < (int64_t)0xFFFFFFFFll;
+  if (per_entry && !hashed)
+    return fail(TC_ERR_CAPACITY, "per-entry plain counts need nnz < 2^32");
   DevBuf<int64_t> ustart;
   if (g->nnz > 0) {
+    if (per_entry)
+      TC_CUDA(cudaMemsetAsync(per_entry, 0, sizeof(uint32_t) * (size_t)g->nnz, s));
     TC_TRY(ustart.alloc(g->n, s));
     launch(k_upper_start, grid_for(g->n, kIsThreads), kIsThreads, 0, s, g->off, g->cols, g->n,
            ustart.p);
     cudaEventRecord(g->ev[4], s);
     if (hashed) {
-      TC_TRY(hash_count(g, 1, ustart.p, nullptr));
+      TC_TRY(hash_count(g, 1, ustart.p, per_entry));
     } else {
       launch(k_plain_intersect, grid_for(g->nnz * 32, kIsThreads, 8), kIsThreads, 0, s, g->erow.p,
              g->nnz, g->off, g->cols, ustart.p, g->ctrl.p + kCtrlWork, g->ctrl.p);

@@ -89,3 +89,36 @@ def test_batch_mixed_recipe_sample(tc):
     counts, status = tc.tc_count_batch([(g.offsets, g.cols) for g in gs], tc.TC_MODE_COVER)
     assert (status == tc.TC_OK).all()
     assert counts.tolist() == [expected(g) for g in gs]
+
+
+def test_batch_union_path(tc):
+    """Members above the batch kernel's limits are packed into one disjoint
+    union and counted together; each count comes from its own range of
+    per-edge counts.  Mixed with tiny members, an invalid large member, and an
+    edgeless member with many vertices, for both modes and both view kinds."""
+    import torch
+    big = [gg.rmat(13, 8, seed=41), gg.rmat(14, 16, seed=42, relabel_seed=7),
+           gg.chung_lu_islands(1 << 14, mean_degree=12, cap=1024, seed=5),
+           gg.complete(200), gg.erdos_renyi(5000, 12 / 4999, 13)]
+    assert all(g.nnz > (1 << 15) for g in big)
+    bad = big[0].cols.copy()
+    bad[100] = big[0].n + 5                               # column out of range
+    empty = gg.CSR(70000, np.zeros(70001, dtype=np.int64), np.zeros(0, dtype=np.uint32))
+    tiny = [gg.complete(6), gg.wheel(9), gg.rmat(8, 8, seed=4)]
+    gs = [big[0], tiny[0], big[1], big[2], tiny[1], big[3], big[4], tiny[2]]
+    items = [(g.offsets, g.cols) for g in gs]
+    items.insert(3, (big[0].offsets, bad))
+    items.append((empty.offsets, empty.cols))
+    want = [expected(g) for g in gs]
+    want.insert(3, 0)
+    want.append(0)
+    want_st = [tc.TC_OK] * len(items)
+    want_st[3] = tc.TC_ERR_INVALID_GRAPH
+    for mode in (tc.TC_MODE_COVER, tc.TC_MODE_PLAIN):
+        counts, status = tc.tc_count_batch(items, mode)
+        assert status.tolist() == want_st
+        assert counts.tolist() == want
+        dev = [(torch.from_numpy(o).cuda(), torch.from_numpy(c).cuda()) for o, c in items]
+        counts, status = tc.tc_count_batch(dev, mode)
+        assert status.tolist() == want_st
+        assert counts.tolist() == want

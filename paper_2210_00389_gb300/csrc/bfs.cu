@@ -1,14 +1,17 @@
 // BFS levels (a1): Def. 2 and Alg. 1 of Bader et al., "Triangle
 // Counting Through Cover-Edges".  L(v) is the shortest distance from the root
 // of v's component.  Alg. 1 restarts a BFS from every unvisited vertex; here
-// every component's root is found first (connected components by lock-free
-// union-find with min-id roots) and one multi-source, level-synchronous BFS
-// runs from all of them at once.  Distances are unique given the roots, so
-// the result equals the sequential restart order's.
+// the restarts are batched.  Distances are unique given the roots, so the
+// result equals the sequential restart order's.
 //
-// Root rule: the maximum-degree vertex (lowest id on ties) roots its
-// component; every other component is rooted at its lowest id.  With an
-// explicit root list, the first listed root of each component roots it.
+// Root rule: the maximum-degree vertex r0 (lowest id on ties) roots its
+// component; every other component is rooted at its lowest id.  That runs in
+// two phases: a BFS from r0 alone, then connected components of the
+// vertices it left unvisited (lock-free union-find with min-id roots, over
+// their edges only) and one multi-source BFS from all of those roots at
+// once.  With an explicit root list, the first listed root of each
+// component roots it: components of the whole graph first, then one
+// multi-source BFS.
 //
 // Each level runs top-down (frontier queue, load-balanced over the
 // frontier's edges, warp-aggregated queue appends) or bottom-up (every
@@ -73,6 +76,52 @@ __global__ void k_cc_flatten(uint32_t n, uint32_t* P) {
   for (; i < (int64_t)n; i += stride) P[i] = uf_find(P, (uint32_t)i);
 }
 
+// Components of the vertices a first BFS left unvisited (a component is
+// either wholly visited or wholly unvisited): parents start at the smallest
+// neighbour, and only edges of unvisited rows are hooked.
+__global__ void k_cc_init_unvisited(const int64_t* __restrict__ off,
+                                    const uint32_t* __restrict__ cols,
+                                    const uint32_t* __restrict__ L, uint32_t n,
+                                    uint32_t* __restrict__ P) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < (int64_t)n; i += stride) {
+    const int64_t b = off[i];
+    uint32_t first = (uint32_t)i;
+    if (L[i] == kUnvisited && off[i + 1] > b) first = cols[b];
+    P[i] = first < (uint32_t)i ? first : (uint32_t)i;
+  }
+}
+
+__global__ void k_cc_hook_unvisited(const uint32_t* __restrict__ erow,
+                                    const uint32_t* __restrict__ cols,
+                                    const uint32_t* __restrict__ L, int64_t nnz, uint32_t* P) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < nnz; i += stride) {
+    uint32_t u = erow[i];
+    if (L[u] != kUnvisited) continue;
+    uint32_t v = cols[i];
+    if (v >= u) continue;
+    while (true) {
+      u = uf_find(P, u);
+      v = uf_find(P, v);
+      if (u == v) break;
+      if (u < v) { uint32_t t = u; u = v; v = t; }
+      if (atomicCAS(&P[u], u, v) == u) break;
+    }
+  }
+}
+
+// Level 0 for the second phase: the lowest id of every unvisited component.
+__global__ void k_levels_unvisited_roots(uint32_t n, const uint32_t* __restrict__ P,
+                                         uint32_t* __restrict__ L) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < (int64_t)n; i += stride)
+    if (L[i] == kUnvisited && P[i] == (uint32_t)i) L[i] = 0u;
+}
+
 // first[c] = smallest index i of a listed root in component c
 __global__ void k_roots_first(const uint32_t* __restrict__ roots, uint32_t nroots,
                               const uint32_t* __restrict__ P, uint32_t* first) {
@@ -119,9 +168,10 @@ __device__ __forceinline__ void queue_append(bool take, uint32_t v, unsigned lon
   if (take) q[base + __popc(mask & ((1u << lane) - 1u))] = v;
 }
 
-// Level-0 queue: every root with at least one neighbour.
+// Level-0 queue: every root with at least one neighbour, except `skip`
+// (a root whose BFS has already run; kUnvisited for none).
 __global__ void k_queue_level0(uint32_t n, const int64_t* __restrict__ off,
-                               const uint32_t* __restrict__ L, uint32_t* q,
+                               const uint32_t* __restrict__ L, uint32_t skip, uint32_t* q,
                                unsigned long long* ctrl) {
   int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -133,7 +183,7 @@ __global__ void k_queue_level0(uint32_t n, const int64_t* __restrict__ off,
     if (i < (int64_t)n && L[i] == 0) {
       root = true;
       d = (unsigned long long)(off[i + 1] - off[i]);
-      take = d > 0;
+      take = d > 0 && (uint32_t)i != skip;
     }
     unsigned rmask = __ballot_sync(0xFFFFFFFFu, root);
     if (lane == 0 && rmask) atomicAdd(&ctrl[kCtrlTmp], (unsigned long long)__popc(rmask));
@@ -219,6 +269,76 @@ __global__ void k_clear_q(unsigned long long* ctrl) {
 }
 
 // ---------------------------------------------------------------- driver
+
+// Queue every level-0 vertex with neighbours (except `skip`) into q; sets
+// g->nroots to the number of level-0 vertices (isolated ones included) and
+// returns the queue's size and edge sum.
+static int level0_queue(tc_graph* g, uint32_t* q, uint32_t skip, int64_t* f, int64_t* mf) {
+  const int T = 256;
+  cudaStream_t s = g->stream;
+  launch(k_clear_q, 1, 1, 0, s, g->ctrl.p);
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlTmp, 0, sizeof(unsigned long long), s));
+  launch(k_queue_level0, grid_for(g->n, T), T, 0, s, g->n, g->off, g->levels.p, skip, q,
+         g->ctrl.p);
+  TC_CUDA(cudaGetLastError());
+  TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s));
+  TC_CUDA(cudaStreamSynchronize(s));
+  *f = (int64_t)g->ctrl_host[kCtrlQ0];
+  *mf = (int64_t)g->ctrl_host[kCtrlQ1];
+  g->nroots = (uint32_t)g->ctrl_host[kCtrlTmp];
+  return TC_OK;
+}
+
+// Level-synchronous BFS from the f vertices of qa (level 0, mf frontier
+// edges); mu = edges of the vertices not yet visited, for the direction
+// heuristic.  *nlev = the number of levels (>= 1); *visited and *edges_seen
+// grow by the vertices and edges reached.  qa / qb are swapped as levels
+// advance.
+static int bfs_run(tc_graph* g, uint32_t*& qa, uint32_t*& qb, unsigned long long* ps, int64_t f,
+                   int64_t mf, int64_t mu, uint32_t* nlev, int64_t* visited, int64_t* edges_seen) {
+  const int T = 256;
+  cudaStream_t s = g->stream;
+  const uint32_t n = g->n;
+  uint32_t* L = g->levels.p;
+  uint32_t cur = 0;
+  bool bottom_up = false;
+  const int64_t alpha = 14, beta = 24;
+  int64_t prev_f = f;
+  while (f > 0) {
+    if (!bottom_up) {
+      if (mf > mu / alpha) bottom_up = true;
+    } else if (f < (int64_t)n / beta && f < prev_f) {
+      bottom_up = false;
+    }
+    launch(k_clear_q, 1, 1, 0, s, g->ctrl.p);
+    if (bottom_up) {
+      launch(k_bfs_bottomup, grid_for(n, T, 16), T, 0, s, n, g->off, g->cols, L, cur, qb, g->ctrl.p);
+      g->stats.bfs_bottom_up++;
+    } else {
+      launch(k_queue_degrees, grid_for(f, T), T, 0, s, qa, f, g->off, ps);
+      TC_TRY(exclusive_scan_u64(ps, f, nullptr, s));
+      launch(k_bfs_topdown, grid_for(mf, T, 16), T, 0, s, qa, f, ps, (unsigned long long)mf, g->off,
+             g->cols, L, cur, qb, g->ctrl.p);
+    }
+    TC_CUDA(cudaGetLastError());
+    TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    g->stats.bfs_levels++;
+    prev_f = f;
+    f = (int64_t)g->ctrl_host[kCtrlQ0];
+    mf = (int64_t)g->ctrl_host[kCtrlQ1];
+    mu -= mf;
+    *visited += f;
+    *edges_seen += mf;
+    if (f > 0) cur++;
+    std::swap(qa, qb);
+  }
+  *nlev = cur + 1;
+  return TC_OK;
+}
+
 int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots) {
   const int T = 256;
   cudaStream_t s = g->stream;
@@ -237,27 +357,59 @@ int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots) {
   TC_TRY(g->levels.reserve(n, s));
   uint32_t* L = g->levels.p;
 
-  // roots: explicit list, or [r0]
-  std::vector<uint32_t> rl;
-  if (roots_host && nroots > 0) {
-    rl.assign(roots_host, roots_host + nroots);
-    for (uint32_t r : rl)
-      if (r >= n) return fail(TC_ERR_INVALID_ARG, "tc_bfs_levels: root %u >= n", r);
-  } else {
-    rl.push_back(g->r0);
-  }
-  DevBuf<uint32_t> P, first, droots, q0, q1;
+  DevBuf<uint32_t> q0, q1;
   DevBuf<unsigned long long> ps;
-  TC_TRY(P.alloc(n, s));
-  TC_TRY(first.alloc(n, s));
-  TC_TRY(droots.alloc(rl.size(), s));
   TC_TRY(q0.alloc(n, s));
   TC_TRY(q1.alloc(n, s));
   TC_TRY(ps.alloc((size_t)n + 1, s));
+  uint32_t* qa = q0.p;
+  uint32_t* qb = q1.p;
+  uint32_t nlev = 0;
+
+  if (!(roots_host && nroots > 0)) {
+    // Default root rule in two phases.  Phase 1: BFS from r0 alone.
+    TC_CUDA(cudaMemsetAsync(L, 0xFF, sizeof(uint32_t) * n, s));
+    TC_CUDA(cudaMemsetAsync(L + g->r0, 0, sizeof(uint32_t), s));
+    const uint32_t r0 = g->r0;
+    TC_CUDA(cudaMemcpyAsync(qa, &r0, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    const int64_t d0 = (int64_t)g->max_degree;
+    int64_t visited = 1, edges_seen = d0;
+    TC_TRY(bfs_run(g, qa, qb, ps.p, d0 > 0 ? 1 : 0, d0, g->nnz - d0, &nlev, &visited, &edges_seen));
+    g->nroots = 1;
+    if (visited < (int64_t)n) {
+      // Phase 2: components of the unvisited vertices (min-id roots), then
+      // one multi-source BFS from all of their roots.
+      DevBuf<uint32_t> P;
+      TC_TRY(P.alloc(n, s));
+      launch(k_cc_init_unvisited, grid_for(n, T), T, 0, s, g->off, g->cols, L, n, P.p);
+      if (g->nnz > 0)
+        launch(k_cc_hook_unvisited, grid_for(g->nnz, T), T, 0, s, g->erow.p, g->cols, L, g->nnz,
+               P.p);
+      launch(k_cc_flatten, grid_for(n, T), T, 0, s, n, P.p);
+      launch(k_levels_unvisited_roots, grid_for(n, T), T, 0, s, n, P.p, L);
+      int64_t f, mf;
+      TC_TRY(level0_queue(g, qa, r0, &f, &mf));
+      uint32_t nlev2 = 0;
+      TC_TRY(bfs_run(g, qa, qb, ps.p, f, mf, g->nnz - edges_seen - mf, &nlev2, &visited,
+                     &edges_seen));
+      nlev = std::max(nlev, nlev2);
+    }
+    g->nlevels = (int64_t)nlev;
+    return TC_OK;
+  }
+
+  // Explicit roots: components of the whole graph, then one multi-source BFS
+  // from the first listed root of each component and the lowest id of every
+  // other component.
+  std::vector<uint32_t> rl(roots_host, roots_host + nroots);
+  for (uint32_t r : rl)
+    if (r >= n) return fail(TC_ERR_INVALID_ARG, "tc_bfs_levels: root %u >= n", r);
+  DevBuf<uint32_t> P, first, droots;
+  TC_TRY(P.alloc(n, s));
+  TC_TRY(first.alloc(n, s));
+  TC_TRY(droots.alloc(rl.size(), s));
   TC_CUDA(cudaMemcpyAsync(droots.p, rl.data(), rl.size() * sizeof(uint32_t),
                           cudaMemcpyHostToDevice, s));
-
-  // components (min-id roots)
   launch(k_cc_init, grid_for(n, T), T, 0, s, g->off, g->cols, n, P.p);
   if (g->nnz > 0) launch(k_cc_hook, grid_for(g->nnz, T), T, 0, s, g->erow.p, g->cols, g->nnz, P.p);
   launch(k_cc_flatten, grid_for(n, T), T, 0, s, n, P.p);
@@ -266,52 +418,11 @@ int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots) {
   launch(k_roots_first, grid_for(nr, T), T, 0, s, droots.p, nr, P.p, first.p);
   launch(k_levels_init, grid_for(n, T), T, 0, s, n, P.p, first.p, L);
   launch(k_levels_roots, grid_for(nr, T), T, 0, s, droots.p, nr, P.p, first.p, L);
-  launch(k_clear_q, 1, 1, 0, s, g->ctrl.p);
-  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlTmp, 0, sizeof(unsigned long long), s));
-  launch(k_queue_level0, grid_for(n, T), T, 0, s, n, g->off, L, q0.p, g->ctrl.p);
-  TC_CUDA(cudaGetLastError());
-  TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
-                          cudaMemcpyDeviceToHost, s));
-  TC_CUDA(cudaStreamSynchronize(s));
-  int64_t f = (int64_t)g->ctrl_host[kCtrlQ0];
-  int64_t mf = (int64_t)g->ctrl_host[kCtrlQ1];
-  int64_t mu = g->nnz - mf;  // edges of still-unvisited vertices
-  g->nroots = (uint32_t)g->ctrl_host[kCtrlTmp];  // level-0 vertices, isolated ones included
-  uint32_t cur = 0;
-  bool bottom_up = false;
-  const int64_t alpha = 14, beta = 24;
-  int64_t prev_f = f;
-  uint32_t* qa = q0.p;
-  uint32_t* qb = q1.p;
-  while (f > 0) {
-    if (!bottom_up) {
-      if (mf > mu / alpha) bottom_up = true;
-    } else if (f < (int64_t)n / beta && f < prev_f) {
-      bottom_up = false;
-    }
-    launch(k_clear_q, 1, 1, 0, s, g->ctrl.p);
-    if (bottom_up) {
-      launch(k_bfs_bottomup, grid_for(n, T, 16), T, 0, s, n, g->off, g->cols, L, cur, qb, g->ctrl.p);
-      g->stats.bfs_bottom_up++;
-    } else {
-      launch(k_queue_degrees, grid_for(f, T), T, 0, s, qa, f, g->off, ps.p);
-      TC_TRY(exclusive_scan_u64(ps.p, f, nullptr, s));
-      launch(k_bfs_topdown, grid_for(mf, T, 16), T, 0, s, qa, f, ps.p, (unsigned long long)mf, g->off,
-                                                       g->cols, L, cur, qb, g->ctrl.p);
-    }
-    TC_CUDA(cudaGetLastError());
-    TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s));
-    TC_CUDA(cudaStreamSynchronize(s));
-    g->stats.bfs_levels++;
-    prev_f = f;
-    f = (int64_t)g->ctrl_host[kCtrlQ0];
-    mf = (int64_t)g->ctrl_host[kCtrlQ1];
-    mu -= mf;
-    if (f > 0) cur++;
-    std::swap(qa, qb);
-  }
-  g->nlevels = (int64_t)cur + 1;
+  int64_t f, mf;
+  TC_TRY(level0_queue(g, qa, kUnvisited, &f, &mf));
+  int64_t visited = 0, edges_seen = 0;
+  TC_TRY(bfs_run(g, qa, qb, ps.p, f, mf, g->nnz - mf, &nlev, &visited, &edges_seen));
+  g->nlevels = (int64_t)nlev;
   return TC_OK;
 }
 

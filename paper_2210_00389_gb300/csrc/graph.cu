@@ -66,22 +66,57 @@ __global__ void k_check_offsets(const int64_t* __restrict__ off, uint32_t n, int
 }
 
 // Warp per vertex: write erow[e] = u for the row, check column range, and,
-// when `strict`, no self-loops and strictly ascending rows.
+// when `strict`, no self-loops and strictly ascending rows.  A row longer
+// than kLongRow is not walked here: the warp lists its chunks (lchunks) and
+// k_rows_long does them, one CTA per chunk.
 __global__ void k_rows_and_check(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                                  uint32_t n, uint32_t* __restrict__ erow, int strict,
-                                 unsigned long long* ctrl) {
+                                 uint2* __restrict__ lchunks, unsigned long long* ctrl) {
   const int lane = threadIdx.x & 31;
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long err = 0;
   for (int64_t u = warp; u < (int64_t)n; u += nwarps) {
     int64_t b = off[u], e = off[u + 1];
+    if (e - b > kLongRow) {
+      const uint32_t nch = (uint32_t)((e - b + kChunk - 1) / kChunk);
+      unsigned long long c0 = 0;
+      if (lane == 0) c0 = atomicAdd(&ctrl[kCtrlLong], (unsigned long long)nch);
+      c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
+      for (uint32_t k = lane; k < nch; k += 32) lchunks[c0 + k] = make_uint2((uint32_t)u, k);
+      continue;
+    }
     for (int64_t i = b + lane; i < e; i += 32) {
       uint32_t v = cols[i];
       erow[i] = (uint32_t)u;
       if (v >= n) err |= kErrColRange;
       if (strict) {
         if (v == (uint32_t)u) err |= kErrSelfLoop;
+        if (i > b && cols[i - 1] >= v) err |= kErrUnsorted;
+      }
+    }
+  }
+  if (err) atomicOr(&ctrl[kCtrlErr], err);
+}
+
+// CTA per chunk of a long row: the same work as k_rows_and_check.
+__global__ void __launch_bounds__(kChunk)
+k_rows_long(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
+            uint32_t* __restrict__ erow, int strict, const uint2* __restrict__ lchunks,
+            unsigned long long* ctrl) {
+  const unsigned long long nch = ctrl[kCtrlLong];
+  unsigned long long err = 0;
+  for (unsigned long long c = blockIdx.x; c < nch; c += gridDim.x) {
+    const uint2 ch = lchunks[c];
+    const uint32_t u = ch.x;
+    const int64_t b = off[u], e = off[u + 1];
+    const int64_t i = b + (int64_t)ch.y * kChunk + threadIdx.x;
+    if (i < e) {
+      const uint32_t v = cols[i];
+      erow[i] = u;
+      if (v >= n) err |= kErrColRange;
+      if (strict) {
+        if (v == u) err |= kErrSelfLoop;
         if (i > b && cols[i - 1] >= v) err |= kErrUnsorted;
       }
     }
@@ -174,9 +209,14 @@ int graph_ingest_checks(tc_graph* g, uint32_t flags) {
   if (g->ctrl_host[kCtrlErr]) return describe_err(g, g->ctrl_host[kCtrlErr]);
 
   TC_TRY(g->erow.alloc((size_t)g->nnz, g->stream));
+  // at most nnz / kChunk full chunks plus one partial chunk per long row
+  TC_TRY(g->lchunks.alloc((size_t)(g->nnz / kChunk + g->nnz / kLongRow + 1), g->stream));
   if (g->n > 0) {
-    launch(k_rows_and_check, grid_for((int64_t)g->n * 32, T, 16), T, 0, g->stream, 
-        g->off, g->cols, g->n, g->erow.p, (flags & TC_GRAPH_VALIDATE) ? 1 : 0, g->ctrl.p);
+    const int strict = (flags & TC_GRAPH_VALIDATE) ? 1 : 0;
+    launch(k_rows_and_check, grid_for((int64_t)g->n * 32, T, 16), T, 0, g->stream, g->off, g->cols,
+           g->n, g->erow.p, strict, g->lchunks.p, g->ctrl.p);
+    launch(k_rows_long, sm_count() * 2, kChunk, 0, g->stream, g->off, g->cols, g->n, g->erow.p,
+           strict, g->lchunks.p, g->ctrl.p);
     TC_CUDA(cudaGetLastError());
   }
   if ((flags & TC_GRAPH_CHECK_SYM) && g->nnz > 0) {
@@ -192,6 +232,7 @@ int graph_ingest_checks(tc_graph* g, uint32_t flags) {
   TC_CUDA(cudaGetLastError());
   TC_TRY(read_ctrl(g));
   if (g->ctrl_host[kCtrlErr]) return describe_err(g, g->ctrl_host[kCtrlErr]);
+  g->nlchunks = (int64_t)g->ctrl_host[kCtrlLong];
   unsigned long long key = g->ctrl_host[kCtrlMax];
   g->max_degree = (uint32_t)(key >> 32);
   g->r0 = g->n > 0 ? 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull) : 0;
@@ -283,6 +324,7 @@ int tc_graph_destroy(tc_graph* g) {
   cudaStreamSynchronize(g->stream);
   graph_drop_cache(g);
   g->erow.release();
+  g->lchunks.release();
   g->cols_own.release();
   g->off_own.release();
   g->ctrl.release();

@@ -28,9 +28,9 @@
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
 // split into work items (owner, slot) of about item_work lookups; a CTA
 // takes an item, builds a bucketized hash table of N(o) in shared memory
-// (4 slots of 4 bytes per bucket, load <= 1/4, usually one 16-byte shared
-// load per lookup) and its warps take the item's edges from a shared counter.
-// Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (six
+// (4 slots per entry, load <= 1/4, in buckets of kSlots slots; usually one
+// shared load per lookup) and its warps take the item's edges from a shared counter.
+// Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (five
 // per SM); larger owners use 1024-thread CTAs with 192 KB tables.  Rows
 // longer than a table (12,288 entries) are processed in windows of
 // consecutive entries (an id range); every probe run keeps a cursor across
@@ -279,36 +279,84 @@ __device__ __forceinline__ uint32_t next_bucket(uint32_t b, uint32_t nb) {
   return b + 1 == nb ? 0u : b + 1;
 }
 
+// Buckets of kSlots 4-byte slots (one 16-, 8- or 4-byte shared load each).
+// The table always has 4 slots per entry (load <= 1/4), so narrower buckets
+// mean more of them: fewer bytes per lookup and fewer bank conflicts, at
+// the price of more overflow into the next bucket.
+constexpr int kSlots = 4;
+template <int S> struct BucketOf;
+template <> struct BucketOf<4> {
+  using T = uint4;
+  __device__ static T none() { return make_uint4(kEmpty, kEmpty, kEmpty, kEmpty); }
+  __device__ static bool has(T q, uint32_t w) { return q.x == w || q.y == w || q.z == w || q.w == w; }
+  __device__ static uint32_t last(T q) { return q.w; }
+};
+template <> struct BucketOf<2> {
+  using T = uint2;
+  __device__ static T none() { return make_uint2(kEmpty, kEmpty); }
+  __device__ static bool has(T q, uint32_t w) { return q.x == w || q.y == w; }
+  __device__ static uint32_t last(T q) { return q.y; }
+};
+template <> struct BucketOf<1> {
+  using T = uint32_t;
+  __device__ static T none() { return kEmpty; }
+  __device__ static bool has(T q, uint32_t w) { return q == w; }
+  __device__ static uint32_t last(T q) { return q; }
+};
+using Bucket = BucketOf<kSlots>;
+using BucketT = Bucket::T;
+
 __device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t nb, uint32_t w) {
   uint32_t b = hash_bucket(w, nb);
   while (true) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (atomicCAS(&tab[4 * b + k], kEmpty, w) == kEmpty) return;
+    for (int k = 0; k < kSlots; ++k)
+      if (atomicCAS(&tab[kSlots * b + k], kEmpty, w) == kEmpty) return;
     b = next_bucket(b, nb);
   }
 }
 
 // Slots of a bucket fill in order and never empty again, so a bucket whose
 // last slot is empty ends the search.
-// Warp-uniform: all 32 lanes call it (valid = false on padding lanes).  One
-// bucket read per lane; a lane whose bucket is full without a match moves to
-// the next bucket, and the loop runs only while some lane still needs one.
-__device__ __forceinline__ unsigned table_find(const uint4* tab4, uint32_t nb, uint32_t w,
-                                               bool valid) {
-  uint32_t b = hash_bucket(w, nb);
-  uint4 q = tab4[b];
-  bool hit = valid && (q.x == w || q.y == w || q.z == w || q.w == w);
-  bool more = valid && !hit && q.w != kEmpty;
-  while (__any_sync(0xFFFFFFFFu, more)) {
-    if (more) {
-      b = next_bucket(b, nb);
-      q = tab4[b];
-      hit = q.x == w || q.y == w || q.z == w || q.w == w;
-      more = !hit && q.w != kEmpty;
+// Warp-uniform: all 32 lanes call it, each with U keys (valid[j] = false on
+// padding).  The U first bucket reads are issued together (lanes with an
+// invalid key read nothing); a key whose bucket is full without a match
+// moves to the next bucket, and that loop runs only while some key of some
+// lane still needs one.  Returns the lane's hits.
+template <int U>
+__device__ __forceinline__ unsigned table_find_n(const BucketT* tab, uint32_t nb,
+                                                 const uint32_t (&w)[U], const bool (&valid)[U]) {
+  uint32_t b[U];
+  BucketT q[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) b[j] = hash_bucket(w[j], nb);
+#pragma unroll
+  for (int j = 0; j < U; ++j) q[j] = valid[j] ? tab[b[j]] : Bucket::none();
+  bool hit[U], more[U];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    hit[j] = valid[j] && Bucket::has(q[j], w[j]);
+    more[j] = valid[j] && !hit[j] && Bucket::last(q[j]) != kEmpty;
+    any |= more[j];
+  }
+  while (__any_sync(0xFFFFFFFFu, any)) {
+    any = false;
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      if (more[j]) {
+        b[j] = next_bucket(b[j], nb);
+        const BucketT r = tab[b[j]];
+        hit[j] = Bucket::has(r, w[j]);
+        more[j] = !hit[j] && Bucket::last(r) != kEmpty;
+        any |= more[j];
+      }
     }
   }
-  return hit ? 1u : 0u;
+  unsigned c = 0;
+#pragma unroll
+  for (int j = 0; j < U; ++j) c += hit[j] ? 1u : 0u;
+  return c;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
@@ -322,7 +370,7 @@ constexpr int kUnroll = 4;  // probe loads in flight per lane
 // taken as one index space of x + end - cut elements), kUnroll loads per
 // lane issued before their lookups.
 __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
-                                              const uint4* tab4, uint32_t nb) {
+                                              const BucketT* tab, uint32_t nb) {
   const int lane = threadIdx.x & 31;
   const uint32_t x = ds.y, shift2 = ds.z - ds.y;  // element k >= x sits at P[k + cut - x]
   const uint32_t total = ds.y + (ds.w - ds.z);
@@ -334,9 +382,10 @@ __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, ui
       const uint32_t k = k0 + j * 32 + lane;
       w[j] = k < total ? __ldg(P + (k < x ? k : k + shift2)) : kEmpty;
     }
+    bool ok[kUnroll];
 #pragma unroll
-    for (int j = 0; j < kUnroll; ++j)
-      c += table_find(tab4, nb, w[j], w[j] != kEmpty);
+    for (int j = 0; j < kUnroll; ++j) ok[j] = w[j] != kEmpty;
+    c += table_find_n<kUnroll>(tab, nb, w, ok);
   }
   return c;
 }
@@ -350,7 +399,7 @@ constexpr uint32_t kBatchMaxWork = 64;  // tasks with fewer lookups share a warp
 // Larger tasks are then done one at a time by the whole warp.
 __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pcols,
                                                 const uint4* __restrict__ descs, uint64_t t0,
-                                                uint32_t nt, const uint4* tab4, uint32_t nb,
+                                                uint32_t nt, const BucketT* tab, uint32_t nb,
                                                 unsigned long long* probes) {
   const int lane = threadIdx.x & 31;
   const uint4 ds = (uint32_t)lane < nt ? descs[t0 + lane] : make_uint4(0u, 0u, 0u, 0u);
@@ -385,9 +434,10 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
       const uint32_t loc = g - eq;
       e[j] = g < total ? __ldg(pcols + base + (loc < xq ? loc : loc + sq)) : kEmpty;
     }
+    bool ok[kUnroll];
 #pragma unroll
-    for (int j = 0; j < kUnroll; ++j)
-      c += table_find(tab4, nb, e[j], e[j] != kEmpty);
+    for (int j = 0; j < kUnroll; ++j) ok[j] = e[j] != kEmpty;
+    c += table_find_n<kUnroll>(tab, nb, e, ok);
   }
   if (lane == 0) *probes += total;
   unsigned big = __ballot_sync(0xFFFFFFFFu, (uint32_t)lane < nt && !small);
@@ -399,7 +449,7 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
     dj.y = __shfl_sync(0xFFFFFFFFu, ds.y, j);
     dj.z = __shfl_sync(0xFFFFFFFFu, ds.z, j);
     dj.w = __shfl_sync(0xFFFFFFFFu, ds.w, j);
-    c += probe_all(pcols + dj.x, dj, tab4, nb);
+    c += probe_all(pcols + dj.x, dj, tab, nb);
     if (lane == 0) *probes += desc_work(dj);
   }
   return c;
@@ -408,8 +458,8 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
 // Look up P[pos..end) while the elements are <= hi (a sorted run); returns
 // the lane's hits and advances pos past the elements looked up.
 __device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict__ P, uint32_t& pos,
-                                                     uint32_t end, uint32_t hi, const uint4* tab4,
-                                                     uint32_t nb) {
+                                                     uint32_t end, uint32_t hi,
+                                                     const BucketT* tab, uint32_t nb) {
   const int lane = threadIdx.x & 31;
   unsigned c = 0;
   while (pos < end) {
@@ -420,12 +470,13 @@ __device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict_
       w[j] = k < end ? __ldg(P + k) : kEmpty;
     }
     uint32_t nin = 0;
+    bool in[kUnroll];
 #pragma unroll
     for (int j = 0; j < kUnroll; ++j) {
-      const bool in = w[j] <= hi;  // kEmpty > hi: padding never counts
-      c += table_find(tab4, nb, w[j], in);
-      nin += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in));
+      in[j] = w[j] <= hi;  // kEmpty > hi: padding never counts
+      nin += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in[j]));
     }
+    c += table_find_n<kUnroll>(tab, nb, w, in);
     pos += nin;  // the elements <= hi form a prefix of the sorted run
     if (nin < 32 * kUnroll) break;
   }
@@ -443,10 +494,11 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  unsigned long long* item_counter, unsigned long long* ctrl) {
   constexpr int kWarps = THREADS / 32;
   constexpr uint32_t kWin = BUCKETS;      // owner entries per table (load <= 1/4)
-  extern __shared__ uint4 tab4[];         // BUCKETS buckets (dynamic shared memory)
+  extern __shared__ uint4 tab4[];         // 4 * BUCKETS slots (dynamic shared memory)
   __shared__ unsigned long long s_item;
   __shared__ unsigned long long s_next;
-  uint32_t* tab = reinterpret_cast<uint32_t*>(tab4);
+  uint32_t* tab32 = reinterpret_cast<uint32_t*>(tab4);
+  const BucketT* tab = reinterpret_cast<const BucketT*>(tab4);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long acc = 0, probes = 0;
   while (true) {
@@ -462,16 +514,21 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
     const int64_t ro = off[o];
     const uint32_t d = (uint32_t)(off[o + 1] - ro);
     const uint32_t nwin = (d + kWin - 1) / kWin;
-    const uint32_t nb = nwin == 1 ? max(32u, d) : (uint32_t)BUCKETS;  // >= 4 slots per entry
+    // the whole table (4 * BUCKETS slots) even for a short row: a lower
+    // load means fewer lookups that overflow into a second bucket, and every
+    // overflow costs the warp another round
+    const uint32_t nq = (uint32_t)BUCKETS;
+    const uint32_t nb = nq * (4 / kSlots);
     for (uint32_t wdx = 0; wdx < nwin; ++wdx) {
       const uint32_t wb = wdx * kWin;
       const uint32_t we = min(d, wb + kWin);
       const uint32_t hi = (wdx + 1 == nwin) ? kEmpty - 1u : cols[ro + we - 1];
-      for (uint32_t k = threadIdx.x; k < nb; k += THREADS)
+      for (uint32_t k = threadIdx.x; k < nq; k += THREADS)
         tab4[k] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
       if (threadIdx.x == 0) s_next = ta;
       __syncthreads();
-      for (uint32_t k = wb + threadIdx.x; k < we; k += THREADS) table_insert(tab, nb, cols[ro + k]);
+      for (uint32_t k = wb + threadIdx.x; k < we; k += THREADS)
+        table_insert(tab32, nb, cols[ro + k]);
       __syncthreads();
       if (BATCH && nwin == 1 && per_edge == nullptr) {
         // warps take 32 edges at a time and share passes over short lists
@@ -481,7 +538,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           t = __shfl_sync(0xFFFFFFFFu, t, 0);
           if (t >= tb) break;
           const uint32_t nt = (uint32_t)min((unsigned long long)32, tb - t);
-          acc += probe_batch(pcols, descs, t, nt, tab4, nb, &probes);
+          acc += probe_batch(pcols, descs, t, nt, tab, nb, &probes);
         }
       } else
       while (true) {
@@ -493,16 +550,16 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         const uint32_t* P = pcols + ds.x;
         unsigned c;
         if (nwin == 1) {
-          c = probe_all(P, ds, tab4, nb);
+          c = probe_all(P, ds, tab, nb);
           if (lane == 0) probes += desc_work(ds);
         } else {
           // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
           const uint32_t z = task_split[t];
           uint4 cur = wdx == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
           const uint32_t p0 = cur.x, p1 = cur.y, p2 = cur.z;
-          c = probe_run_window(P, cur.x, ds.y, hi, tab4, nb);
-          c += probe_run_window(P, cur.y, z, hi, tab4, nb);
-          c += probe_run_window(P, cur.z, ds.w, hi, tab4, nb);
+          c = probe_run_window(P, cur.x, ds.y, hi, tab, nb);
+          c += probe_run_window(P, cur.y, z, hi, tab, nb);
+          c += probe_run_window(P, cur.z, ds.w, hi, tab, nb);
           if (lane == 0) {
             probes += (cur.x - p0) + (cur.y - p1) + (cur.z - p2);
             if (wdx + 1 < nwin) cursors[t] = cur;
@@ -536,9 +593,9 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
 }
 
 // Table configurations: medium owners (degree <= kMediumMax) in 256-thread
-// CTAs with 32 KB tables, six per SM; large owners in 1024-thread CTAs with
-// 192 KB tables (windows of 24,576 entries), one per SM.
-constexpr int kMedThreads = 256, kMedBuckets = 2048, kMedPerSM = 6;
+// CTAs with 32 KB tables, five per SM; large owners in 1024-thread CTAs with
+// 192 KB tables (windows of 12,288 entries), one per SM.
+constexpr int kMedThreads = 256, kMedBuckets = 2048, kMedPerSM = 5;
 constexpr int kBigThreads = 1024, kBigBuckets = 12288, kBigPerSM = 1;
 static_assert(kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
 

@@ -16,6 +16,15 @@ namespace tc {
 constexpr uint32_t kUnvisited = 0xFFFFFFFFu;
 constexpr int kWarp = 32;
 
+// Rows with more than kLongRow entries are not given to one warp: at ingest
+// they are cut into chunks of kChunk consecutive entries, listed in
+// tc_graph::lchunks as {row, chunk number within the row}; the chunks of a
+// row are contiguous in the list, so chunk c of row u sits at index
+// (index of u's first chunk) + c.  Kernels over rows skip long rows and
+// take their chunks with one CTA per chunk instead.
+constexpr int64_t kLongRow = 1024;
+constexpr int kChunk = 1024;
+
 // ---------------------------------------------------------------- errors
 // Record a message for tc_last_error() and return `status`.
 int fail(int status, const char* fmt, ...);
@@ -110,6 +119,8 @@ struct tc_graph {
   tc::DevBuf<int64_t> off_own;
   tc::DevBuf<uint32_t> cols_own;
   tc::DevBuf<uint32_t> erow;  // row id of every CSR entry (COO rows)
+  tc::DevBuf<uint2> lchunks;  // chunks of the rows longer than kLongRow
+  int64_t nlchunks = 0;
 
   // cached BFS levels
   tc::DevBuf<uint32_t> levels;
@@ -150,6 +161,7 @@ enum CtrlSlot {
   kCtrlTmp = 7,
   kCtrlWork = 8,      // dynamic work counter of the intersection kernels
   kCtrlItems = 9,     // work items per table class (two slots: 9, 10)
+  kCtrlLong = 11,     // chunks of long rows (ingest)
   kCtrlSlots = 16
 };
 

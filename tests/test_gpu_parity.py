@@ -91,6 +91,21 @@ def test_chung_lu_islands_small(tc):
     check_graph(tc, g)
 
 
+@pytest.mark.parametrize("name", ["union", "relabelled"])
+def test_long_rows(tc, name):
+    """Rows at and around the chunking threshold (1,024 entries per row, in
+    chunks of 1,024): exactly 1,024, 1,025 (a one-entry last chunk), 2,048,
+    2,049 and 2,400 entries, each at several positions in the vertex order."""
+    g = gg.disjoint_union(gg.star(1024), gg.wheel(1025), gg.friendship(1024),
+                          gg.wheel(2049), gg.complete(1101), gg.star(1025),
+                          gg.rmat(9, 8, seed=3))
+    degs = set(np.diff(g.offsets).tolist())
+    assert {1024, 1025, 2048, 2049, 1100} <= degs
+    if name == "relabelled":
+        g = gg.relabel(g, 12345)
+    check_graph(tc, g)
+
+
 def test_erdos_renyi_and_unions(tc):
     check_graph(tc, gg.erdos_renyi(3000, 0.004, 5))
     check_graph(tc, gg.disjoint_union(gg.rmat(10, 8, seed=3), gg.empty(100),

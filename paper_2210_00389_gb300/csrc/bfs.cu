@@ -93,22 +93,33 @@ __global__ void k_cc_init_unvisited(const int64_t* __restrict__ off,
   }
 }
 
-__global__ void k_cc_hook_unvisited(const uint32_t* __restrict__ erow,
+// Warp per group of 32 vertices: the unvisited ones with edges are hooked
+// one row at a time by the whole warp.
+__global__ void k_cc_hook_unvisited(const int64_t* __restrict__ off,
                                     const uint32_t* __restrict__ cols,
-                                    const uint32_t* __restrict__ L, int64_t nnz, uint32_t* P) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (; i < nnz; i += stride) {
-    uint32_t u = erow[i];
-    if (L[u] != kUnvisited) continue;
-    uint32_t v = cols[i];
-    if (v >= u) continue;
-    while (true) {
-      u = uf_find(P, u);
-      v = uf_find(P, v);
-      if (u == v) break;
-      if (u < v) { uint32_t t = u; u = v; v = t; }
-      if (atomicCAS(&P[u], u, v) == u) break;
+                                    const uint32_t* __restrict__ L, uint32_t n, uint32_t* P) {
+  const int lane = threadIdx.x & 31;
+  int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; base < (int64_t)n; base += stride) {
+    const int64_t x = base + lane;
+    const bool want = x < (int64_t)n && L[x] == kUnvisited && off[x + 1] > off[x];
+    unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+    while (m) {
+      const uint32_t u0 = (uint32_t)base + (uint32_t)(__ffs(m) - 1);
+      m &= m - 1;
+      const int64_t b = off[u0], e = off[u0 + 1];
+      for (int64_t i = b + lane; i < e; i += 32) {
+        uint32_t u = u0, v = cols[i];
+        if (v >= u) continue;
+        while (true) {
+          u = uf_find(P, u);
+          v = uf_find(P, v);
+          if (u == v) break;
+          if (u < v) { uint32_t t = u; u = v; v = t; }
+          if (atomicCAS(&P[u], u, v) == u) break;
+        }
+      }
     }
   }
 }
@@ -383,8 +394,7 @@ int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots) {
       TC_TRY(P.alloc(n, s));
       launch(k_cc_init_unvisited, grid_for(n, T), T, 0, s, g->off, g->cols, L, n, P.p);
       if (g->nnz > 0)
-        launch(k_cc_hook_unvisited, grid_for(g->nnz, T), T, 0, s, g->erow.p, g->cols, L, g->nnz,
-               P.p);
+        launch(k_cc_hook_unvisited, grid_for(n, T), T, 0, s, g->off, g->cols, L, n, P.p);
       launch(k_cc_flatten, grid_for(n, T), T, 0, s, n, P.p);
       launch(k_levels_unvisited_roots, grid_for(n, T), T, 0, s, n, P.p, L);
       int64_t f, mf;

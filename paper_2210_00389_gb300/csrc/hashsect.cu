@@ -28,11 +28,12 @@
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
 // split into work items (owner, slot) of about item_work lookups; a CTA
 // takes an item, builds a bucketized hash table of N(o) in shared memory
-// (4 slots per entry, load <= 1/4, in buckets of kSlots slots; usually one
-// shared load per lookup) and its warps take the item's edges from a shared counter.
+// (the CTA's whole table, in buckets of kSlots slots, load <= 1/2; usually
+// one shared load per lookup) and its warps take the item's edges from a
+// shared counter.
 // Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (five
-// per SM); larger owners use 1024-thread CTAs with 192 KB tables.  Rows
-// longer than a table (12,288 entries) are processed in windows of
+// per SM); larger owners use 1024-thread CTAs with 224 KB tables.  Rows
+// longer than a window (kBigWin entries) are processed in windows of
 // consecutive entries (an id range); every probe run keeps a cursor across
 // windows, so each probe element is looked up once.
 #include <algorithm>
@@ -131,6 +132,7 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
   for (; base < nidx; base += stride) {
     const uint64_t idx = base + lane;
     bool small = false;
+    uint32_t key = kEmpty, work = 0;  // owner of a hashed edge, its lookups + 1
     if (idx < nidx) {
       uint32_t u, v;
       if (edge_at<M>(s, idx, u, v)) {
@@ -139,10 +141,21 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
         if (dout <= kSmallOwner) {
           small = true;
         } else {
-          const uint4 d = probe_desc<M>(s, idx, u, v, p);
-          atomicAdd(&owner_cnt[o], 1u);
-          atomicAdd(&owner_work[o], (unsigned long long)desc_work(d) + 1ull);
+          key = o;
+          work = desc_work(probe_desc<M>(s, idx, u, v, p)) + 1u;
         }
+      }
+    }
+    // lanes with the same owner (consecutive edges often share one) add
+    // their counts with one atomic per owner
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    if (key != kEmpty) {
+      // 16-bit halves, so the sum of 32 values cannot wrap
+      const unsigned hi = __reduce_add_sync(peers, work >> 16);
+      const unsigned lo = __reduce_add_sync(peers, work & 0xFFFFu);
+      if (lane == __ffs(peers) - 1) {
+        atomicAdd(&owner_cnt[key], (uint32_t)__popc(peers));
+        atomicAdd(&owner_work[key], ((unsigned long long)hi << 16) + lo);
       }
     }
     const unsigned m = __ballot_sync(0xFFFFFFFFu, small);
@@ -177,21 +190,27 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
   for (; base < nidx; base += stride) {
     const uint64_t idx = base + lane;
     bool light = false;
-    uint32_t u, v;
+    uint32_t u, v, o = 0, p = 0, key = kEmpty;
     if (idx < nidx && edge_at<M>(s, idx, u, v)) {
-      uint32_t o, p, dout;
+      uint32_t dout;
       owner_probe(s.off, u, v, o, p, dout);
       if (dout > kSmallOwner) {
-        if (owner_hashed(owner_work[o], dout)) {
-          const unsigned long long t = ostart[o] + atomicAdd(&cursor[o], 1u);
-          const uint4 d = probe_desc<M>(s, idx, u, v, p);
-          descs[t] = d;
-          task_split[t] = probe_split<M>(s, p, d);
-          if (task_idx) task_idx[t] = (uint32_t)idx;
-        } else {
-          light = true;
-        }
+        if (owner_hashed(owner_work[o], dout)) key = o;
+        else light = true;
       }
+    }
+    // one cursor atomic per owner among the warp's lanes
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    if (key != kEmpty) {
+      const int leader = __ffs(peers) - 1;
+      uint32_t c0 = 0;
+      if (lane == leader) c0 = atomicAdd(&cursor[key], (uint32_t)__popc(peers));
+      c0 = __shfl_sync(peers, c0, leader);
+      const unsigned long long t = ostart[key] + c0 + __popc(peers & ((1u << lane) - 1u));
+      const uint4 d = probe_desc<M>(s, idx, u, v, p);
+      descs[t] = d;
+      task_split[t] = probe_split<M>(s, p, d);
+      if (task_idx) task_idx[t] = (uint32_t)idx;
     }
     const unsigned m = __ballot_sync(0xFFFFFFFFu, light);
     if (m) {
@@ -483,7 +502,7 @@ __device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict_
   return c;
 }
 
-template <int M, int THREADS, int BUCKETS, int MINB, bool BATCH>
+template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                  const uint32_t* __restrict__ pcols, const uint2* __restrict__ items,
@@ -493,7 +512,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  uint4* __restrict__ cursors, uint32_t* __restrict__ per_edge,
                  unsigned long long* item_counter, unsigned long long* ctrl) {
   constexpr int kWarps = THREADS / 32;
-  constexpr uint32_t kWin = BUCKETS;      // owner entries per table (load <= 1/4)
+  constexpr uint32_t kWin = WIN;          // owner entries per table window
   extern __shared__ uint4 tab4[];         // 4 * BUCKETS slots (dynamic shared memory)
   __shared__ unsigned long long s_item;
   __shared__ unsigned long long s_next;
@@ -594,12 +613,19 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
 
 // Table configurations: medium owners (degree <= kMediumMax) in 256-thread
 // CTAs with 32 KB tables, five per SM; large owners in 1024-thread CTAs with
-// 192 KB tables (windows of 12,288 entries), one per SM.
+// 224 KB tables, one per SM.
 constexpr int kMedThreads = 256, kMedBuckets = 2048, kMedPerSM = 5;
-constexpr int kBigThreads = 1024, kBigBuckets = 12288, kBigPerSM = 1;
+constexpr int kBigThreads = 1024, kBigBuckets = 14336, kBigPerSM = 1;
+// Owner entries per table window, per mode (cover, plain): every owner row
+// longer than this is processed in windows, and each window pass revisits
+// all the owner's edges, so a larger window (at a higher table load, more
+// lookups overflowing into a second bucket) can pay.  Tuned on R-MAT scale
+// 20 and 22.
+constexpr int kMedWin = kMedBuckets;
+constexpr int kBigWin[2] = {14336, 28672};
 static_assert(kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
 
-template <int M, int THREADS, int BUCKETS, int MINB, bool BATCH>
+template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH>
 static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, uint64_t nitems,
                        const unsigned long long* ostart, const uint32_t* owner_cnt,
                        const uint4* descs, const uint32_t* task_split, const uint32_t* task_idx,
@@ -607,7 +633,7 @@ static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, u
   if (nitems == 0) return TC_OK;
   cudaStream_t st = g->stream;
   const size_t smem = sizeof(uint4) * BUCKETS;
-  auto k = k_hash_intersect<M, THREADS, BUCKETS, MINB, BATCH>;
+  auto k = k_hash_intersect<M, THREADS, BUCKETS, WIN, MINB, BATCH>;
   TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TC_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   const uint64_t grid = std::min<uint64_t>((uint64_t)sm_count() * MINB, nitems);
@@ -673,10 +699,10 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   }
   TC_CUDA(cudaGetLastError());
   cudaEventRecord(g->ev[6], st);  // end of bucketing
-  TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigPerSM, false>(
+  TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigWin[M], kBigPerSM, false>(
       g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge, counters.p + 2)));
-  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedPerSM, false>(
+  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedWin, kMedPerSM, false>(
       g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge, counters.p + 3)));
   cudaEventRecord(g->ev[7], st);  // end of the hash kernels

@@ -166,7 +166,7 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  uint4* __restrict__ seg) {
   constexpr int kW = kChunk / 32;
   __shared__ unsigned s_tot[2][3][kW];   // [before this chunk / whole row][segment][warp]
-  __shared__ unsigned s_wc[4][kW];       // per warp and segment: entries in this chunk
+  __shared__ unsigned s_wc[4][kW];       // per segment and warp: entries before this warp
   __shared__ unsigned s_base[2][3];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -216,6 +216,18 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
           if (lane == 0) s_base[h][j] = v;
         }
+    } else if (wid <= 4) {
+      // exclusive scan over the warps of segment wid - 1's counts
+      const int j = wid - 1;
+      const unsigned x = s_wc[j][lane];
+      unsigned v = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += y;
+      }
+      __syncwarp();
+      s_wc[j][lane] = v - x;
     }
     __syncthreads();
     if (cls >= 0) {
@@ -230,9 +242,7 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         // earlier chunks' entries above the level: their size minus the rest
         before = ch.y * (unsigned)kChunk - s_base[0][0] - s_base[0][1] - s_base[0][2];
       }
-      unsigned inw = 0;
-      for (int k = 0; k < wid; ++k) inw += s_wc[cls][k];
-      scols[b + start + before + inw + __popc(m[cls] & lt)] = w;
+      scols[b + start + before + s_wc[cls][wid] + __popc(m[cls] & lt)] = w;
     }
     if (ch.y == 0 && threadIdx.x == 0) {
       const unsigned R0 = s_base[1][0], R1 = s_base[1][1], R2 = s_base[1][2];

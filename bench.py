@@ -50,8 +50,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "rmat10", "rmat18", "rmat20", "chunglu23", "batch",
-                             "serve"])
+                    choices=["rmat22", "rmat10", "rmat18", "rmat20", "rmat26", "chunglu23",
+                             "batch", "serve"])
     ap.add_argument("--requests", type=int, default=20000, help="serve: stream length")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
     ap.add_argument("--serve-scale", type=int, default=26, help="serve: resident R-MAT scale")
@@ -72,6 +72,11 @@ def make_graph(workload: str, rank: int):
         seed = 2 + rank * 1000
         g = gg.rmat(22, 16, seed, relabel_seed=seed + 2**32)
         desc = ("R-MAT scale 22, edgefactor 16, a/b/c/d=.57/.19/.19/.05, edge seed %d, "
+                "relabel stream %d+2^32, symmetrised, deduplicated" % (seed, seed))
+    elif workload == "rmat26":
+        seed = 5 + rank * 1000
+        g = gg.rmat(26, 16, seed, relabel_seed=seed + 2**32)
+        desc = ("R-MAT scale 26, edgefactor 16, a/b/c/d=.57/.19/.19/.05, edge seed %d, "
                 "relabel stream %d+2^32, symmetrised, deduplicated" % (seed, seed))
     elif workload in ("rmat18", "rmat20"):
         sc = int(workload[4:])

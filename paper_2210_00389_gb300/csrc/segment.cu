@@ -36,137 +36,218 @@ __device__ __forceinline__ int seg_class(uint32_t w, uint32_t lw, uint32_t x, ui
   return lw < lx ? 0 : (lw == lx ? (w < x ? 1 : 2) : 3);
 }
 
-// Warp per row (rows of at most kLongRow entries); each chunk of 32 entries
-// is classified, and warp ballots give each entry's rank inside its
-// segment.  A row of at most 32 entries takes one pass; a longer one counts
-// its segments first.
+constexpr int kTinyRow = 8;  // rows this short are partitioned by one thread
+constexpr int kSegUnroll = 4;
+constexpr int kSegBlock = 32 * kSegUnroll;  // entries a warp loads at once
+
+// Entries [base, base + kSegBlock) of a row ending at e: lane entries
+// base + 32 k + lane with their segment class (-1 past the row).
+__device__ __forceinline__ void seg_load_block(const uint32_t* __restrict__ cols,
+                                               const uint32_t* __restrict__ L, int64_t base,
+                                               int64_t e, uint32_t x, uint32_t lx,
+                                               uint32_t (&w)[kSegUnroll], int (&cls)[kSegUnroll]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kSegUnroll; ++k) {
+    const int64_t i = base + 32 * k + lane;
+    w[k] = i < e ? cols[i] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kSegUnroll; ++k) {
+    const int64_t i = base + 32 * k + lane;
+    cls[k] = i < e ? seg_class(w[k], L[w[k]], x, lx) : -1;
+  }
+}
+
+// Rows of at most kLongRow entries.  A warp takes 32 consecutive rows: each
+// lane partitions its own row if it has at most kTinyRow entries (all its
+// loads issued at once); the longer rows are then taken one at a time by
+// the whole warp, in blocks of kSegBlock entries classified and ranked
+// inside their segment by warp ballots.  A row of one block takes one pass;
+// a longer one counts its segments first.
 __global__ void __launch_bounds__(kSegThreads)
 k_segment_rows(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                const uint32_t* __restrict__ L, uint32_t n, uint32_t* __restrict__ scols,
                uint4* __restrict__ seg) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t x = warp; x < (int64_t)n; x += nwarps) {
-    const int64_t b = off[x], e = off[x + 1];
-    if (e - b > kLongRow) continue;  // chunked: k_segment_chunks
-    const uint32_t lx = L[x];
-    unsigned c0, c1, c2;
-    if (e - b <= 32) {
-      const int64_t i = b + lane;
-      uint32_t w = 0;
-      int cls = -1;
-      if (i < e) {
-        w = cols[i];
-        cls = seg_class(w, L[w], (uint32_t)x, lx);
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t gbase = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; gbase < (int64_t)n;
+       gbase += gstride) {
+    const int64_t xl = gbase + lane;
+    int64_t bl = 0, el = 0;
+    if (xl < (int64_t)n) {
+      bl = off[xl];
+      el = off[xl + 1];
+    }
+    const int64_t dl = el - bl;
+    if (xl < (int64_t)n && dl <= kTinyRow) {
+      const uint32_t lx = L[xl];
+      uint32_t w[kTinyRow];
+      int cls[kTinyRow];
+#pragma unroll
+      for (int k = 0; k < kTinyRow; ++k) w[k] = k < dl ? cols[bl + k] : 0u;
+#pragma unroll
+      for (int k = 0; k < kTinyRow; ++k)
+        cls[k] = k < dl ? seg_class(w[k], L[w[k]], (uint32_t)xl, lx) : -1;
+      unsigned c0 = 0, c1 = 0, c2 = 0;
+#pragma unroll
+      for (int k = 0; k < kTinyRow; ++k) {
+        c0 += cls[k] == 0;
+        c1 += cls[k] == 1;
+        c2 += cls[k] == 2;
       }
-      const unsigned m0 = __ballot_sync(0xFFFFFFFFu, cls == 0);
-      const unsigned m1 = __ballot_sync(0xFFFFFFFFu, cls == 1);
-      const unsigned m2 = __ballot_sync(0xFFFFFFFFu, cls == 2);
-      const unsigned m3 = __ballot_sync(0xFFFFFFFFu, cls == 3);
-      c0 = __popc(m0);
-      c1 = __popc(m1);
-      c2 = __popc(m2);
-      if (cls == 0) scols[b + __popc(m0 & lt)] = w;
-      else if (cls == 1) scols[b + c0 + __popc(m1 & lt)] = w;
-      else if (cls == 2) scols[b + c0 + c1 + __popc(m2 & lt)] = w;
-      else if (cls == 3) scols[b + c0 + c1 + c2 + __popc(m3 & lt)] = w;
-    } else {
-      // pass 1: segment sizes
-      c0 = 0; c1 = 0; c2 = 0;
-      for (int64_t i = b + lane; i < e; i += 32) {
-        const uint32_t w = cols[i];
-        const int cls = seg_class(w, L[w], (uint32_t)x, lx);
-        c0 += cls == 0;
-        c1 += cls == 1;
-        c2 += cls == 2;
+      int64_t p0 = bl, p1 = bl + c0, p2 = bl + c0 + c1, p3 = bl + c0 + c1 + c2;
+#pragma unroll
+      for (int k = 0; k < kTinyRow; ++k) {
+        if (cls[k] == 0) scols[p0++] = w[k];
+        else if (cls[k] == 1) scols[p1++] = w[k];
+        else if (cls[k] == 2) scols[p2++] = w[k];
+        else if (cls[k] == 3) scols[p3++] = w[k];
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        c0 += __shfl_xor_sync(0xFFFFFFFFu, c0, o);
-        c1 += __shfl_xor_sync(0xFFFFFFFFu, c1, o);
-        c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
+      seg[xl] = make_uint4(c0, c0 + c1, c0 + c1 + c2, 0u);
+    }
+    // rows for the whole warp (long rows are chunked: k_segment_chunks)
+    unsigned rows = __ballot_sync(0xFFFFFFFFu, xl < (int64_t)n && dl > kTinyRow && dl <= kLongRow);
+    while (rows) {
+      const int r = __ffs(rows) - 1;
+      rows &= rows - 1;
+      const int64_t x = gbase + r;
+      const int64_t b = __shfl_sync(0xFFFFFFFFu, bl, r), e = __shfl_sync(0xFFFFFFFFu, el, r);
+      const uint32_t lx = L[x];
+      // blocks of kSegBlock entries, all loads of a block issued together
+      unsigned c0 = 0, c1 = 0, c2 = 0;
+      if (e - b > kSegBlock) {
+        // pass 1: segment sizes (a row of one block counts from its ballots)
+        for (int64_t base = b; base < e; base += kSegBlock) {
+          uint32_t w[kSegUnroll];
+          int cls[kSegUnroll];
+          seg_load_block(cols, L, base, e, (uint32_t)x, lx, w, cls);
+#pragma unroll
+          for (int k = 0; k < kSegUnroll; ++k) {
+            c0 += cls[k] == 0;
+            c1 += cls[k] == 1;
+            c2 += cls[k] == 2;
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          c0 += __shfl_xor_sync(0xFFFFFFFFu, c0, o);
+          c1 += __shfl_xor_sync(0xFFFFFFFFu, c1, o);
+          c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
+        }
       }
       // pass 2: stable scatter into the four runs
       int64_t p0 = b, p1 = b + c0, p2 = b + c0 + c1, p3 = b + c0 + c1 + c2;
-      for (int64_t base = b; base < e; base += 32) {
-        const int64_t i = base + lane;
-        uint32_t w = 0;
-        int cls = -1;
-        if (i < e) {
-          w = cols[i];
-          cls = seg_class(w, L[w], (uint32_t)x, lx);
+      for (int64_t base = b; base < e; base += kSegBlock) {
+        uint32_t w[kSegUnroll];
+        int cls[kSegUnroll];
+        seg_load_block(cols, L, base, e, (uint32_t)x, lx, w, cls);
+        unsigned m[kSegUnroll][4];
+#pragma unroll
+        for (int k = 0; k < kSegUnroll; ++k)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) m[k][j] = __ballot_sync(0xFFFFFFFFu, cls[k] == j);
+        if (e - b <= kSegBlock) {
+          // one block: the segment sizes are its ballot counts
+#pragma unroll
+          for (int k = 0; k < kSegUnroll; ++k) {
+            c0 += __popc(m[k][0]);
+            c1 += __popc(m[k][1]);
+            c2 += __popc(m[k][2]);
+          }
+          p1 = b + c0;
+          p2 = b + c0 + c1;
+          p3 = b + c0 + c1 + c2;
         }
-        const unsigned m0 = __ballot_sync(0xFFFFFFFFu, cls == 0);
-        const unsigned m1 = __ballot_sync(0xFFFFFFFFu, cls == 1);
-        const unsigned m2 = __ballot_sync(0xFFFFFFFFu, cls == 2);
-        const unsigned m3 = __ballot_sync(0xFFFFFFFFu, cls == 3);
-        if (cls == 0) scols[p0 + __popc(m0 & lt)] = w;
-        else if (cls == 1) scols[p1 + __popc(m1 & lt)] = w;
-        else if (cls == 2) scols[p2 + __popc(m2 & lt)] = w;
-        else if (cls == 3) scols[p3 + __popc(m3 & lt)] = w;
-        p0 += __popc(m0);
-        p1 += __popc(m1);
-        p2 += __popc(m2);
-        p3 += __popc(m3);
+#pragma unroll
+        for (int k = 0; k < kSegUnroll; ++k) {
+          if (cls[k] == 0) scols[p0 + __popc(m[k][0] & lt)] = w[k];
+          else if (cls[k] == 1) scols[p1 + __popc(m[k][1] & lt)] = w[k];
+          else if (cls[k] == 2) scols[p2 + __popc(m[k][2] & lt)] = w[k];
+          else if (cls[k] == 3) scols[p3 + __popc(m[k][3] & lt)] = w[k];
+          p0 += __popc(m[k][0]);
+          p1 += __popc(m[k][1]);
+          p2 += __popc(m[k][2]);
+          p3 += __popc(m[k][3]);
+        }
       }
+      if (lane == 0) seg[x] = make_uint4(c0, c0 + c1, c0 + c1 + c2, 0u);
     }
-    if (lane == 0) seg[x] = make_uint4(c0, c0 + c1, c0 + c1 + c2, 0u);
   }
 }
 
-// Long rows, pass 1: CTA per chunk, the chunk's segment sizes.
-__global__ void __launch_bounds__(kChunk)
+// Long rows: a CTA of kChunkThreads threads per chunk of kChunk entries,
+// kChunkPer entries per thread (entry s * kChunkThreads + thread), all of a
+// thread's loads issued before they are used.
+constexpr int kChunkThreads = 256;
+constexpr int kChunkPer = kChunk / kChunkThreads;
+constexpr int kChunkWarps = kChunkThreads / 32;
+static_assert(kChunkPer * kChunkWarps == 32, "one warp scans a chunk's (sub-chunk, warp) counts");
+
+// Long rows, pass 1: the chunk's segment sizes.
+__global__ void __launch_bounds__(kChunkThreads)
 k_segment_chunk_counts(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                        const uint32_t* __restrict__ L, const uint2* __restrict__ lchunks,
                        int64_t nch, uint4* __restrict__ ccnt) {
-  __shared__ unsigned red[3][kChunk / 32];
+  __shared__ unsigned red[3][kChunkWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
     const uint2 ch = lchunks[c];
     const uint32_t x = ch.x, lx = L[x];
-    const int64_t b = off[x], e = off[x + 1];
-    const int64_t i = b + (int64_t)ch.y * kChunk + threadIdx.x;
-    int cls = -1;
-    if (i < e) {
-      const uint32_t w = cols[i];
-      cls = seg_class(w, L[w], x, lx);
+    const int64_t e = off[x + 1];
+    const int64_t i0 = off[x] + (int64_t)ch.y * kChunk + threadIdx.x;
+    uint32_t w[kChunkPer];
+#pragma unroll
+    for (int k = 0; k < kChunkPer; ++k) {
+      const int64_t i = i0 + k * kChunkThreads;
+      w[k] = i < e ? cols[i] : kUnvisited;
     }
-    const unsigned m0 = __ballot_sync(0xFFFFFFFFu, cls == 0);
-    const unsigned m1 = __ballot_sync(0xFFFFFFFFu, cls == 1);
-    const unsigned m2 = __ballot_sync(0xFFFFFFFFu, cls == 2);
+    unsigned a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int k = 0; k < kChunkPer; ++k) {
+      if (w[k] != kUnvisited) {
+        const int cls = seg_class(w[k], L[w[k]], x, lx);
+        a0 += cls == 0;
+        a1 += cls == 1;
+        a2 += cls == 2;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xFFFFFFFFu, a0, o);
+      a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, o);
+      a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, o);
+    }
     if (lane == 0) {
-      red[0][wid] = __popc(m0);
-      red[1][wid] = __popc(m1);
-      red[2][wid] = __popc(m2);
+      red[0][wid] = a0;
+      red[1][wid] = a1;
+      red[2][wid] = a2;
     }
     __syncthreads();
-    if (wid == 0) {
-      unsigned a0 = red[0][lane], a1 = red[1][lane], a2 = red[2][lane];
-      for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xFFFFFFFFu, a0, o);
-        a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, o);
-        a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, o);
+    if (threadIdx.x == 0) {
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      for (int k = 0; k < kChunkWarps; ++k) {
+        q.x += red[0][k];
+        q.y += red[1][k];
+        q.z += red[2][k];
       }
-      if (lane == 0) ccnt[c] = make_uint4(a0, a1, a2, 0u);
+      ccnt[c] = q;
     }
     __syncthreads();
   }
 }
 
-// Long rows, pass 2: CTA per chunk.  The row's segment sizes and the
-// chunk's offset inside each segment are sums over the row's chunk counts
-// (the row's chunks are contiguous in lchunks); then a stable scatter of
-// the chunk, ranked by warp ballots and a scan over the CTA's warps.  The
-// row's first chunk writes seg.
-__global__ void __launch_bounds__(kChunk)
+// Long rows, pass 2.  The row's segment sizes and the chunk's offset inside
+// each segment are sums over the row's chunk counts (the row's chunks are
+// contiguous in lchunks); then a stable scatter of the chunk, ranked by
+// __match_any_sync inside a warp and a scan over the chunk's (sub-chunk,
+// warp) counts.  The row's first chunk writes seg.
+__global__ void __launch_bounds__(kChunkThreads)
 k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                  const uint32_t* __restrict__ L, const uint2* __restrict__ lchunks, int64_t nch,
                  const uint4* __restrict__ ccnt, uint32_t* __restrict__ scols,
                  uint4* __restrict__ seg) {
-  constexpr int kW = kChunk / 32;
-  __shared__ unsigned s_tot[2][3][kW];   // [before this chunk / whole row][segment][warp]
-  __shared__ unsigned s_wc[4][kW];       // per segment and warp: entries before this warp
+  __shared__ unsigned s_tot[2][3][kChunkWarps];  // [before this chunk / whole row][segment][warp]
+  __shared__ unsigned s_cnt[4][32];  // [segment][sub-chunk * warps + warp]: then exclusive scan
   __shared__ unsigned s_base[2][3];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -176,9 +257,18 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
     const int64_t b = off[x], e = off[x + 1];
     const uint32_t nrow = (uint32_t)((e - b + kChunk - 1) / kChunk);
     const int64_t first = c - ch.y;
+    // this thread's entries (loads first)
+    const int64_t i0 = b + (int64_t)ch.y * kChunk + threadIdx.x;
+    uint32_t w[kChunkPer];
+    int cls[kChunkPer];
+#pragma unroll
+    for (int k = 0; k < kChunkPer; ++k) {
+      const int64_t i = i0 + k * kChunkThreads;
+      w[k] = i < e ? cols[i] : kUnvisited;
+    }
     // row totals and this chunk's prefix
     unsigned t[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    for (uint32_t k = threadIdx.x; k < nrow; k += kChunk) {
+    for (uint32_t k = threadIdx.x; k < nrow; k += kChunkThreads) {
       const uint4 q = ccnt[first + k];
       t[1][0] += q.x; t[1][1] += q.y; t[1][2] += q.z;
       if (k < ch.y) { t[0][0] += q.x; t[0][1] += q.y; t[0][2] += q.z; }
@@ -191,20 +281,24 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
         if (lane == 0) s_tot[h][j][wid] = v;
       }
-    // classify this thread's entry
-    const int64_t i = b + (int64_t)ch.y * kChunk + threadIdx.x;
-    uint32_t w = 0;
-    int cls = -1;
-    if (i < e) {
-      w = cols[i];
-      cls = seg_class(w, L[w], x, lx);
-    }
-    unsigned m[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) m[j] = __ballot_sync(0xFFFFFFFFu, cls == j);
-    if (lane == 0) {
+    for (int k = 0; k < kChunkPer; ++k)
+      cls[k] = w[k] != kUnvisited ? seg_class(w[k], L[w[k]], x, lx) : -1;
+    unsigned rank[kChunkPer];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) s_wc[j][wid] = __popc(m[j]);
+    for (int k = 0; k < kChunkPer; ++k) {
+      rank[k] = __popc(__match_any_sync(0xFFFFFFFFu, cls[k]) & lt);
+      const unsigned m0 = __ballot_sync(0xFFFFFFFFu, cls[k] == 0);
+      const unsigned m1 = __ballot_sync(0xFFFFFFFFu, cls[k] == 1);
+      const unsigned m2 = __ballot_sync(0xFFFFFFFFu, cls[k] == 2);
+      const unsigned m3 = __ballot_sync(0xFFFFFFFFu, cls[k] == 3);
+      if (lane == 0) {
+        const int slot = k * kChunkWarps + wid;
+        s_cnt[0][slot] = __popc(m0);
+        s_cnt[1][slot] = __popc(m1);
+        s_cnt[2][slot] = __popc(m2);
+        s_cnt[3][slot] = __popc(m3);
+      }
     }
     __syncthreads();
     if (wid == 0) {
@@ -212,42 +306,39 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-          unsigned v = s_tot[h][j][lane];
+          unsigned v = lane < kChunkWarps ? s_tot[h][j][lane] : 0u;
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
           if (lane == 0) s_base[h][j] = v;
         }
     } else if (wid <= 4) {
-      // exclusive scan over the warps of segment wid - 1's counts
+      // exclusive scan of segment (wid - 1)'s counts in (sub-chunk, warp) order
       const int j = wid - 1;
-      const unsigned x = s_wc[j][lane];
-      unsigned v = x;
+      const unsigned v0 = s_cnt[j][lane];
+      unsigned v = v0;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const unsigned y = __shfl_up_sync(0xFFFFFFFFu, v, o);
         if (lane >= o) v += y;
       }
       __syncwarp();
-      s_wc[j][lane] = v - x;
+      s_cnt[j][lane] = v - v0;
     }
     __syncthreads();
-    if (cls >= 0) {
+    const unsigned R0 = s_base[1][0], R1 = s_base[1][1], R2 = s_base[1][2];
+#pragma unroll
+    for (int k = 0; k < kChunkPer; ++k) {
+      const int cl = cls[k];
+      if (cl < 0) continue;
       // segment start in the row + entries of this segment in earlier
-      // chunks + in earlier warps of this chunk + rank in the warp
-      const unsigned R0 = s_base[1][0], R1 = s_base[1][1], R2 = s_base[1][2];
-      unsigned start = cls == 0 ? 0u : (cls == 1 ? R0 : (cls == 2 ? R0 + R1 : R0 + R1 + R2));
-      unsigned before;
-      if (cls < 3) {
-        before = s_base[0][cls];
-      } else {
-        // earlier chunks' entries above the level: their size minus the rest
-        before = ch.y * (unsigned)kChunk - s_base[0][0] - s_base[0][1] - s_base[0][2];
-      }
-      scols[b + start + before + s_wc[cls][wid] + __popc(m[cls] & lt)] = w;
+      // chunks + in earlier (sub-chunk, warp) groups + rank in the warp
+      const unsigned start = cl == 0 ? 0u : (cl == 1 ? R0 : (cl == 2 ? R0 + R1 : R0 + R1 + R2));
+      // earlier chunks' entries above the level: their size minus the rest
+      const unsigned before =
+          cl < 3 ? s_base[0][cl]
+                 : ch.y * (unsigned)kChunk - s_base[0][0] - s_base[0][1] - s_base[0][2];
+      scols[b + start + before + s_cnt[cl][k * kChunkWarps + wid] + rank[k]] = w[k];
     }
-    if (ch.y == 0 && threadIdx.x == 0) {
-      const unsigned R0 = s_base[1][0], R1 = s_base[1][1], R2 = s_base[1][2];
-      seg[x] = make_uint4(R0, R0 + R1, R0 + R1 + R2, 0u);
-    }
+    if (ch.y == 0 && threadIdx.x == 0) seg[x] = make_uint4(R0, R0 + R1, R0 + R1 + R2, 0u);
     __syncthreads();
   }
 }
@@ -262,24 +353,54 @@ __global__ void k_cover_counts(const uint4* __restrict__ seg, uint32_t n,
   }
 }
 
-// Warp per vertex: copy the "same level, id > u" segment of u into H.
-// Long rows are copied by k_cover_gather_chunks.
+// Copy the "same level, id > u" segment of every u into H.  A warp takes 32
+// consecutive vertices: a lane copies its own vertex's run if it has at
+// most kTinyRow entries; longer runs are copied by the whole warp, one at a
+// time.  Long rows are copied by k_cover_gather_chunks.
 __global__ void __launch_bounds__(kSegThreads)
 k_cover_gather(const int64_t* __restrict__ off, const uint32_t* __restrict__ scols,
                const uint4* __restrict__ seg, const unsigned long long* __restrict__ hoff,
                uint32_t n, uint2* __restrict__ H) {
   const int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = warp; u < (int64_t)n; u += nwarps) {
-    const int64_t b = off[u];
-    if (off[u + 1] - b > kLongRow) continue;
-    const uint4 s = seg[u];
-    const int64_t len = (int64_t)(s.z - s.y);
-    if (len == 0) continue;
-    const uint32_t* src = scols + b + s.y;
-    const unsigned long long dst = hoff[u];
-    for (int64_t k = lane; k < len; k += 32) H[dst + k] = make_uint2((uint32_t)u, src[k]);
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t gbase = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; gbase < (int64_t)n;
+       gbase += gstride) {
+    const int64_t u = gbase + lane;
+    bool mine = false, warp_run = false;
+    int64_t src = 0;
+    uint32_t len = 0;
+    unsigned long long dst = 0;
+    if (u < (int64_t)n) {
+      const int64_t b = off[u];
+      if (off[u + 1] - b <= kLongRow) {
+        const uint4 sg = seg[u];
+        len = sg.z - sg.y;
+        if (len > 0) {
+          src = b + sg.y;
+          dst = hoff[u];
+          mine = len <= kTinyRow;
+          warp_run = !mine;
+        }
+      }
+    }
+    if (mine) {
+      uint32_t w[kTinyRow];
+#pragma unroll
+      for (int k = 0; k < kTinyRow; ++k) w[k] = k < (int)len ? scols[src + k] : 0u;
+#pragma unroll
+      for (int k = 0; k < kTinyRow; ++k)
+        if (k < (int)len) H[dst + k] = make_uint2((uint32_t)u, w[k]);
+    }
+    unsigned runs = __ballot_sync(0xFFFFFFFFu, warp_run);
+    while (runs) {
+      const int r = __ffs(runs) - 1;
+      runs &= runs - 1;
+      const int64_t s0 = __shfl_sync(0xFFFFFFFFu, src, r);
+      const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, len, r);
+      const unsigned long long d0 = __shfl_sync(0xFFFFFFFFu, dst, r);
+      const uint32_t ur = (uint32_t)(gbase + r);
+      for (uint32_t k = lane; k < l0; k += 32) H[d0 + k] = make_uint2(ur, scols[s0 + k]);
+    }
   }
 }
 
@@ -310,11 +431,11 @@ int compute_segments(tc_graph* g) {
   if (g->nlchunks > 0) {
     DevBuf<uint4> ccnt;
     TC_TRY(ccnt.alloc((size_t)g->nlchunks, s));
-    const int grid = (int)std::min<int64_t>(g->nlchunks, (int64_t)sm_count() * 2);
-    launch(k_segment_chunk_counts, grid, kChunk, 0, s, g->off, g->cols, g->levels.p,
+    const int grid = (int)std::min<int64_t>(g->nlchunks, (int64_t)sm_count() * 8);
+    launch(k_segment_chunk_counts, grid, kChunkThreads, 0, s, g->off, g->cols, g->levels.p,
            g->lchunks.p, g->nlchunks, ccnt.p);
-    launch(k_segment_chunks, grid, kChunk, 0, s, g->off, g->cols, g->levels.p, g->lchunks.p,
-           g->nlchunks, ccnt.p, g->scols.p, g->seg.p);
+    launch(k_segment_chunks, grid, kChunkThreads, 0, s, g->off, g->cols, g->levels.p,
+           g->lchunks.p, g->nlchunks, ccnt.p, g->scols.p, g->seg.p);
   }
   TC_CUDA(cudaGetLastError());
   g->seg_valid = true;

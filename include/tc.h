@@ -164,6 +164,28 @@ TC_API int tc_count(tc_graph* g, int mode, uint64_t* count_out);
  * counts_out: host/device uint32[cap].  TC_ERR_CAPACITY if |H| > cap. */
 TC_API int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap);
 
+/* Shards of the count for several GPUs (the CSR and the levels replicated on
+ * each; every GPU counts one contiguous slice; the slice counts add up to T).
+ * The count is a sum of independent per-edge terms over the mode's edge
+ * index space -- cover: the cover edges in tc_cover_edges order (Alg. 1,
+ * Thm. 2); plain: the CSR entries, those with u > v adding nothing.
+ *
+ * tc_shard_bounds: bounds_out (host int64[nshards + 1]) receives
+ * 0 = b_0 <= b_1 <= ... <= b_nshards = |edges|, chosen so that the slices
+ * [b_k, b_k+1) carry about equal estimated work (sum over their edges of
+ * min(d(u), d(v)) + 1); inner bounds are multiples of 4,096 or |edges|.
+ * Runs the BFS and the cover extraction first if they are not cached
+ * (cover mode).
+ * Errors: TC_ERR_INVALID_ARG (NULL, unknown mode, nshards < 1), TC_ERR_OOM,
+ * TC_ERR_CUDA.
+ *
+ * tc_count_range: *count_out (host) = the sum of the per-edge terms of the
+ * edges [begin, end) (0 <= begin <= end <= |edges|, else TC_ERR_INVALID_ARG);
+ * an empty range counts 0.  Summed over the slices of any partition of
+ * [0, |edges|) the counts equal tc_count's. */
+TC_API int tc_shard_bounds(tc_graph* g, int mode, int32_t nshards, int64_t* bounds_out);
+TC_API int tc_count_range(tc_graph* g, int mode, int64_t begin, int64_t end, uint64_t* count_out);
+
 /* Timings (device ms, CUDA events on the graph's stream) of the most recent
  * tc_count / tc_bfs_levels / tc_cover_edges call, per stage, and work sizes. */
 typedef struct {

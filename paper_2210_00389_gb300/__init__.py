@@ -103,6 +103,8 @@ _SIGS = {
     "tc_cover_edges": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _i64p]),
     "tc_count": (ctypes.c_int, [_vp, ctypes.c_int, _u64p]),
     "tc_cover_edge_counts": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
+    "tc_shard_bounds": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int32, _vp]),
+    "tc_count_range": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _u64p]),
     "tc_count_plain_static": (ctypes.c_int, [_vp, _vp, ctypes.c_uint32, ctypes.c_int64, _vp, _vp]),
     "tc_count_batch": (ctypes.c_int, [ctypes.POINTER(CSRView), ctypes.c_int32, ctypes.c_int,
                                       ctypes.POINTER(Options), _vp, _u64p, _ip]),
@@ -274,6 +276,19 @@ def tc_count(g: int, mode: int = TC_MODE_COVER) -> int:
     return c.value
 
 
+def tc_shard_bounds(g: int, mode: int, nshards: int) -> np.ndarray:
+    """int64[nshards + 1] work-balanced bounds of the mode's edge index space."""
+    b = np.zeros(nshards + 1, dtype=np.int64)
+    _check(_lib.tc_shard_bounds(g, mode, nshards, b.ctypes.data), "tc_shard_bounds")
+    return b
+
+
+def tc_count_range(g: int, mode: int, begin: int, end: int) -> int:
+    c = ctypes.c_uint64(0)
+    _check(_lib.tc_count_range(g, mode, begin, end, ctypes.byref(c)), "tc_count_range")
+    return c.value
+
+
 def tc_cover_edge_counts(g: int, out=None):
     cnt = ctypes.c_int64(0)
     _check(_lib.tc_cover_edges(g, None, 0, ctypes.byref(cnt)), "tc_cover_edges")
@@ -403,6 +418,12 @@ class Graph:
 
     def levels(self, roots=None, out=None):
         return tc_bfs_levels(self.handle, roots, out)
+
+    def shard_bounds(self, mode: int, nshards: int) -> np.ndarray:
+        return tc_shard_bounds(self.handle, mode, nshards)
+
+    def count_range(self, mode: int, begin: int, end: int) -> int:
+        return tc_count_range(self.handle, mode, begin, end)
 
     def cover_edges(self, out=None):
         return tc_cover_edges(self.handle, out)

@@ -106,6 +106,38 @@ int tc_count(tc_graph* g, int mode, uint64_t* count_out) {
   return TC_OK;
 }
 
+int tc_shard_bounds(tc_graph* g, int mode, int32_t nshards, int64_t* bounds_out) {
+  if (!g || !bounds_out) return fail(TC_ERR_INVALID_ARG, "tc_shard_bounds: NULL argument");
+  if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
+    return fail(TC_ERR_INVALID_ARG, "tc_shard_bounds: unknown mode %d", mode);
+  if (nshards < 1) return fail(TC_ERR_INVALID_ARG, "tc_shard_bounds: nshards < 1");
+  DeviceGuard dg(g->device);
+  if (mode == TC_MODE_COVER && g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
+  return shard_bounds(g, mode, nshards, bounds_out);
+}
+
+int tc_count_range(tc_graph* g, int mode, int64_t begin, int64_t end, uint64_t* count_out) {
+  if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_count_range: NULL argument");
+  if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
+    return fail(TC_ERR_INVALID_ARG, "tc_count_range: unknown mode %d", mode);
+  DeviceGuard dg(g->device);
+  if (mode == TC_MODE_COVER) {
+    if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
+    if (g->num_cover < 0) TC_TRY(compute_cover(g));
+  }
+  const int64_t m = mode == TC_MODE_COVER ? g->num_cover : g->nnz;
+  if (begin < 0 || end < begin || end > m)
+    return fail(TC_ERR_INVALID_ARG, "tc_count_range: [%lld, %lld) not within [0, %lld]",
+                (long long)begin, (long long)end, (long long)m);
+  uint64_t T = 0;
+  if (end > begin) {
+    if (mode == TC_MODE_COVER) TC_TRY(count_cover(g, nullptr, &T, begin, end));
+    else TC_TRY(count_plain(g, &T, nullptr, begin, end));
+  }
+  *count_out = T;
+  return TC_OK;
+}
+
 int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap) {
   if (!g || !counts_out) return fail(TC_ERR_INVALID_ARG, "tc_cover_edge_counts: NULL argument");
   DeviceGuard dg(g->device);

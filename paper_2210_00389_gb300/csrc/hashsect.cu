@@ -61,6 +61,7 @@ struct EdgeSrc {
   const int64_t* ustart;
   const int64_t* off;
   const uint32_t* cols;
+  uint64_t first;  // edge index of local index 0 (a shard's first edge)
 };
 
 // Decode edge `idx`: returns false for plain entries that are not u < v.
@@ -130,19 +131,19 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
   uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (; base < nidx; base += stride) {
-    const uint64_t idx = base + lane;
+    const uint64_t idx = base + lane, gi = s.first + idx;
     bool small = false;
     uint32_t key = kEmpty, work = 0;  // owner of a hashed edge, its lookups + 1
     if (idx < nidx) {
       uint32_t u, v;
-      if (edge_at<M>(s, idx, u, v)) {
+      if (edge_at<M>(s, gi, u, v)) {
         uint32_t o, p, dout;
         owner_probe(s.off, u, v, o, p, dout);
         if (dout <= kSmallOwner) {
           small = true;
         } else {
           key = o;
-          work = desc_work(probe_desc<M>(s, idx, u, v, p)) + 1u;
+          work = desc_work(probe_desc<M>(s, gi, u, v, p)) + 1u;
         }
       }
     }
@@ -164,7 +165,7 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
       unsigned long long b0 = 0;
       if (lane == leader) b0 = atomicAdd(&ctrl[kCtrlQ0], (unsigned long long)__popc(m));
       b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
-      if (small) small_list[b0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
+      if (small) small_list[b0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)gi;
     }
   }
 }
@@ -188,10 +189,10 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
   uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (; base < nidx; base += stride) {
-    const uint64_t idx = base + lane;
+    const uint64_t idx = base + lane, gi = s.first + idx;
     bool light = false;
     uint32_t u, v, o = 0, p = 0, key = kEmpty;
-    if (idx < nidx && edge_at<M>(s, idx, u, v)) {
+    if (idx < nidx && edge_at<M>(s, gi, u, v)) {
       uint32_t dout;
       owner_probe(s.off, u, v, o, p, dout);
       if (dout > kSmallOwner) {
@@ -207,10 +208,10 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
       if (lane == leader) c0 = atomicAdd(&cursor[key], (uint32_t)__popc(peers));
       c0 = __shfl_sync(peers, c0, leader);
       const unsigned long long t = ostart[key] + c0 + __popc(peers & ((1u << lane) - 1u));
-      const uint4 d = probe_desc<M>(s, idx, u, v, p);
+      const uint4 d = probe_desc<M>(s, gi, u, v, p);
       descs[t] = d;
       task_split[t] = probe_split<M>(s, p, d);
-      if (task_idx) task_idx[t] = (uint32_t)idx;
+      if (task_idx) task_idx[t] = (uint32_t)gi;
     }
     const unsigned m = __ballot_sync(0xFFFFFFFFu, light);
     if (m) {
@@ -218,7 +219,7 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
       unsigned long long b0 = 0;
       if (lane == leader) b0 = atomicAdd(&ctrl[kCtrlQ0], (unsigned long long)__popc(m));
       b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
-      if (light) small_list[b0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
+      if (light) small_list[b0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)gi;
     }
   }
 }
@@ -713,23 +714,27 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   return TC_OK;
 }
 
-// Requires |edges| < 2^32 and nnz < 2^32 (32-bit task indices and row
-// positions); callers fall back to the merge kernels otherwise.
-int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge) {
+// Edges [first, last) of the mode's index space (cover: H; plain: CSR
+// entries, those with u > v skipped).  Requires |edges| < 2^32 and
+// nnz < 2^32 (32-bit task indices and row positions); callers fall back to
+// the merge kernels otherwise.
+int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge, int64_t first,
+               int64_t last) {
   EdgeSrc s{};
   s.off = g->off;
   s.cols = g->cols;
+  s.first = (uint64_t)first;
+  if (last <= first) return TC_OK;
+  const uint64_t nidx = (uint64_t)(last - first);
   if (mode == kModeCover) {
     s.H = g->cover.p;
     s.hoff = g->hoff.p;
     s.seg = g->seg.p;
-    if (g->num_cover == 0) return TC_OK;
-    return hash_count_mode<kModeCover>(g, s, (uint64_t)g->num_cover, g->scols.p, ustart, per_edge);
+    return hash_count_mode<kModeCover>(g, s, nidx, g->scols.p, ustart, per_edge);
   }
   s.erow = g->erow.p;
   s.ustart = ustart;
-  if (g->nnz == 0) return TC_OK;
-  return hash_count_mode<kModePlain>(g, s, (uint64_t)g->nnz, g->cols, ustart, per_edge);
+  return hash_count_mode<kModePlain>(g, s, nidx, g->cols, ustart, per_edge);
 }
 
 }  // namespace tc

@@ -179,8 +179,18 @@ enum : unsigned long long {
 int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots);
 int compute_segments(tc_graph* g);
 int compute_cover(tc_graph* g);
-int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total);
-int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry = nullptr);
+// Counts over the edge range [first, last) of the mode's index space (cover:
+// H in its canonical order; plain: CSR entries, those with u > v adding
+// nothing); last < 0 means to the end.  Per-edge outputs are indexed by the
+// global edge index.
+int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t first = 0,
+                int64_t last = -1);
+int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry = nullptr, int64_t first = 0,
+                int64_t last = -1);
+
+// Work-balanced shard bounds of the mode's edge index space (shard.cu):
+// bounds_host[0] = 0 <= ... <= bounds_host[P] = |edges|.
+int shard_bounds(tc_graph* g, int mode, int32_t P, int64_t* bounds_host);
 
 // Exclusive scan of `n` 64-bit counts in place on `stream`; returns the
 // total through `total_dev` (device pointer, may be null).

@@ -208,7 +208,8 @@ k_plain_intersect(const uint32_t* __restrict__ erow, int64_t nnz, const int64_t*
   block_add(elems, &ctrl[kCtrlElems]);
 }
 
-int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge);
+int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge, int64_t first,
+               int64_t last);
 
 // Stage timings: ev4 -> ev6 bucketing, ev6 -> ev7 hash kernel, ev7 -> ev5
 // small-owner merge (the merge-only fallback records ev6 = ev7 = ev4).
@@ -227,21 +228,33 @@ static void finish_stats(tc_graph* g, bool hashed) {
   cudaGetLastError();  // a timing query that failed must not leak into later checks
 }
 
-int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
+// The merge kernels take work from ctrl[kCtrlWork] until it reaches their
+// bound, so a range [first, last) starts the counter at first.
+static int set_work_start(tc_graph* g, int64_t first) {
+  const unsigned long long v = (unsigned long long)first;
+  TC_CUDA(cudaMemcpyAsync(g->ctrl.p + kCtrlWork, &v, sizeof(v), cudaMemcpyHostToDevice, g->stream));
+  return TC_OK;
+}
+
+int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t first,
+                int64_t last) {
   cudaStream_t s = g->stream;
   if (g->num_cover < 0) TC_TRY(compute_cover(g));
+  if (last < 0 || last > g->num_cover) last = g->num_cover;
+  if (first < 0) first = 0;
+  if (first > last) first = last;
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
-  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
+  TC_TRY(set_work_start(g, first));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
   if (per_edge_out && g->num_cover > 0)
     TC_CUDA(cudaMemsetAsync(per_edge_out, 0, sizeof(uint32_t) * (size_t)g->num_cover, s));
   const bool hashed = g->num_cover < (int64_t)0xFFFFFFFFll && g->nnz < (int64_t)0xFFFFFFFFll;
   cudaEventRecord(g->ev[4], s);
   if (hashed) {
-    TC_TRY(hash_count(g, 0, nullptr, per_edge_out));
-  } else {
-    launch(k_cover_intersect, grid_for(g->num_cover * 32, kIsThreads, 8), kIsThreads, 0, s,
-           g->cover.p, g->num_cover, g->off, g->scols.p, g->seg.p, g->hoff.p, per_edge_out,
+    TC_TRY(hash_count(g, 0, nullptr, per_edge_out, first, last));
+  } else if (last > first) {
+    launch(k_cover_intersect, grid_for((last - first) * 32, kIsThreads, 8), kIsThreads, 0, s,
+           g->cover.p, last, g->off, g->scols.p, g->seg.p, g->hoff.p, per_edge_out,
            g->ctrl.p + kCtrlWork, g->ctrl.p);
     TC_CUDA(cudaGetLastError());
   }
@@ -250,24 +263,27 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total) {
                           cudaMemcpyDeviceToHost, s));
   TC_CUDA(cudaStreamSynchronize(s));
   *total = g->ctrl_host[kCtrlCount];
-  g->stats.edges_intersected = g->num_cover;
-  finish_stats(g, hashed && g->num_cover > 0);
+  g->stats.edges_intersected = last - first;
+  finish_stats(g, hashed && last > first);
   return TC_OK;
 }
 
 // per_entry (device, nnz entries, or NULL): the count of every CSR entry
-// (u, v) with u < v; other entries are left 0.
-int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry) {
+// (u, v) with u < v; other entries are left 0.  Entries [first, last).
+int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry, int64_t first, int64_t last) {
   cudaStream_t s = g->stream;
+  if (last < 0 || last > g->nnz) last = g->nnz;
+  if (first < 0) first = 0;
+  if (first > last) first = last;
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
-  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
+  TC_TRY(set_work_start(g, first));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
   g->stats.ms_intersect = g->stats.ms_bucket = g->stats.ms_main_kernel = 0.f;
   const bool hashed = g->nnz < (int64_t)0xFFFFFFFFll;
   if (per_entry && !hashed)
     return fail(TC_ERR_CAPACITY, "per-entry plain counts need nnz < 2^32");
   DevBuf<int64_t> ustart;
-  if (g->nnz > 0) {
+  if (last > first) {
     if (per_entry)
       TC_CUDA(cudaMemsetAsync(per_entry, 0, sizeof(uint32_t) * (size_t)g->nnz, s));
     TC_TRY(ustart.alloc(g->n, s));
@@ -275,10 +291,10 @@ int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry) {
            ustart.p);
     cudaEventRecord(g->ev[4], s);
     if (hashed) {
-      TC_TRY(hash_count(g, 1, ustart.p, per_entry));
+      TC_TRY(hash_count(g, 1, ustart.p, per_entry, first, last));
     } else {
-      launch(k_plain_intersect, grid_for(g->nnz * 32, kIsThreads, 8), kIsThreads, 0, s, g->erow.p,
-             g->nnz, g->off, g->cols, ustart.p, g->ctrl.p + kCtrlWork, g->ctrl.p);
+      launch(k_plain_intersect, grid_for((last - first) * 32, kIsThreads, 8), kIsThreads, 0, s,
+             g->erow.p, last, g->off, g->cols, ustart.p, g->ctrl.p + kCtrlWork, g->ctrl.p);
       TC_CUDA(cudaGetLastError());
     }
     cudaEventRecord(g->ev[5], s);
@@ -287,8 +303,8 @@ int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry) {
                           cudaMemcpyDeviceToHost, s));
   TC_CUDA(cudaStreamSynchronize(s));
   *total = g->ctrl_host[kCtrlCount];
-  g->stats.edges_intersected = g->nnz / 2;
-  if (g->nnz > 0) finish_stats(g, hashed);
+  g->stats.edges_intersected = (last - first) / 2;
+  if (last > first) finish_stats(g, hashed);
   return TC_OK;
 }
 

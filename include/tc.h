@@ -232,7 +232,12 @@ typedef struct {
   int32_t blocks_per_sm;   /* resident blocks per SM (1..16) */
   int32_t skew;            /* warp merge when the longer list is <= skew x the shorter,
                               else binary search of the shorter in the longer (>= 2) */
-  int32_t reserved[5];
+  int32_t tiny_max_nnz;    /* graphs with at most this many CSR entries (and at most
+                              65,536 vertices) go to the persistent per-graph kernel;
+                              larger ones are packed into one disjoint union counted by
+                              the single-graph pipeline (0 = built-in 32,768; at most
+                              2^22) */
+  int32_t reserved[4];
 } tc_options;
 
 /* Count ngraphs independent graphs in one persistent, CUDA-graph-captured
@@ -246,23 +251,32 @@ TC_API int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mode,
 
 /* ---------------------------------------------------------------- serving */
 /* A request loop on the current device (no paper counterpart: a systems form
- * of Alg. 1).  Requests are admitted in arrival order while fewer than
- * `slots` are in flight and their estimated device bytes fit the budget next
- * to the resident graphs.  Admitted small one-shot graphs (n <= 65,536,
- * nnz <= 2^20) are grouped and counted together with tc_count_batch each time
- * the batch worker is free (continuous batching); resident and large
+ * of Alg. 1).  Small one-shot graphs (n <= 65,536, nnz <= 2^20) and the
+ * other requests (large one-shot graphs, requests on resident graphs) wait
+ * in two queues, each admitted in arrival order: a small request as soon as
+ * its estimated device bytes fit the budget next to the resident graphs and
+ * the requests in flight, another request when, in addition, fewer than
+ * `slots` of its kind are in flight.  Admitted small graphs are grouped and
+ * counted together with tc_count_batch each time the batch worker is free
+ * (continuous batching, on a high-priority stream); resident and large
  * requests run on worker threads with their own streams, so requests overlap
  * on the device.  Counts are the same exact integers as tc_count's. */
 typedef struct tc_server tc_server;
 typedef struct {
   size_t hbm_budget_bytes; /* admission limit for resident + in-flight graphs */
-  int32_t slots;           /* max requests in flight on the device (> 0) */
+  int32_t slots;           /* max large or resident requests in flight (> 0) */
   int32_t queue_capacity;  /* max queued, not yet admitted requests (<= 0: 4096) */
   int32_t wait_limit_ms;   /* a request not admitted within this time finishes
                               with TC_ERR_TIMEOUT (<= 0: 10000) */
-  int32_t reserved[4];     /* reserved[0] = k > 0: test hook, the k-th admitted
-                              request fails with TC_ERR_OOM as if its device
-                              allocation had failed; others must be 0 */
+  int32_t fail_admitted;   /* test hook: k > 0 makes the k-th admitted request fail
+                              with TC_ERR_OOM as if its device allocation had
+                              failed; 0 = off */
+  int32_t borrow_views;    /* 0: tc_serve_submit copies a one-shot CSR before it
+                              returns.  1: it keeps the caller's pointers, which
+                              must stay valid and unchanged until tc_serve_poll
+                              reports the request done (or tc_serve_destroy
+                              returns): no copy on the submitting thread */
+  int32_t reserved[2];     /* must be 0 */
 } tc_serve_config;
 
 /* Start the scheduler and worker threads.  TC_ERR_INVALID_ARG for a NULL
@@ -274,8 +288,9 @@ TC_API int tc_serve_create(const tc_serve_config* cfg, tc_server** out);
  * tc_graph_create with TC_GRAPH_VALIDATE. */
 TC_API int tc_serve_register(tc_server* s, const tc_csr_view* csr, uint64_t* graph_id);
 /* Queue a count request (mode TC_MODE_COVER or TC_MODE_PLAIN) on a resident
- * graph (csr_or_null == NULL) or on a one-shot CSR (host or device view,
- * copied before return, so the caller's buffers are free afterwards).
+ * graph (csr_or_null == NULL) or on a one-shot CSR (host or device view;
+ * copied before return, so the caller's buffers are free afterwards, unless
+ * the server borrows views -- see tc_serve_config.borrow_views).
  * Errors: TC_ERR_AGAIN (queue full), TC_ERR_OOM (the request alone exceeds
  * the budget), TC_ERR_NOT_FOUND (unknown graph id), TC_ERR_CANCELLED
  * (shutting down), TC_ERR_INVALID_ARG. */

@@ -72,13 +72,15 @@ class Stats(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("skew", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("skew", ctypes.c_int32), ("tiny_max_nnz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class ServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("slots", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("fail_admitted", ctypes.c_int32), ("borrow_views", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 _vp = ctypes.c_void_p
@@ -319,7 +321,8 @@ def autotuned_options() -> Options | None:
     try:
         import json
         b = json.load(open(path))["batch"]
-        return Options(int(b["block_threads"]), int(b["blocks_per_sm"]), int(b["skew"]))
+        return Options(int(b["block_threads"]), int(b["blocks_per_sm"]), int(b["skew"]),
+                       int(b.get("tiny_max_nnz", 0)))
     except (OSError, KeyError, ValueError):
         return None
 
@@ -343,11 +346,14 @@ def tc_count_batch(graphs, mode: int = TC_MODE_COVER, opt: Options | None = None
 
 
 def tc_serve_create(hbm_budget_bytes: int, slots: int = 64, queue_capacity: int = 4096,
-                    wait_limit_ms: int = 0, fail_request: int = 0) -> int:
+                    wait_limit_ms: int = 0, fail_request: int = 0,
+                    borrow_views: bool = False) -> int:
     """``fail_request`` = k > 0 injects a host-side allocation failure into the
-    k-th admitted request (tests of failure handling)."""
-    res = (ctypes.c_int32 * 4)(fail_request, 0, 0, 0)
-    cfg = ServeConfig(hbm_budget_bytes, slots, queue_capacity, wait_limit_ms, res)
+    k-th admitted request (tests of failure handling).  With ``borrow_views``
+    the server keeps the submitted arrays instead of copying them: the caller
+    keeps them alive and unchanged until the request is reported done."""
+    cfg = ServeConfig(hbm_budget_bytes, slots, queue_capacity, wait_limit_ms, fail_request,
+                      1 if borrow_views else 0, (ctypes.c_int32 * 2)(0, 0))
     h = _vp()
     _check(_lib.tc_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "tc_serve_create")
     return h.value

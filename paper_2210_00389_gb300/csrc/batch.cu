@@ -30,7 +30,7 @@
 namespace tc {
 
 constexpr uint32_t kBatchMaxN = 1u << 16;     // vertices per graph in the batch kernel
-constexpr int64_t kBatchMaxNnz = 1ll << 15;   // entries per graph in the batch kernel
+constexpr int64_t kBatchMaxNnz = 1ll << 15;   // entries per graph (default; tc_options)
 
 struct BGraph {
   const int64_t* off;
@@ -555,18 +555,26 @@ extern "C" int tc_count_batch(const tc_csr_view* graphs, int32_t ngraphs, int mo
     return fail(TC_ERR_INVALID_ARG, "tc_count_batch: block_threads must be 128, 256 or 512");
   if (per_sm > 16) per_sm = 16;
   const int64_t skew = opt && opt->skew >= 2 ? opt->skew : kSkew;
+  int64_t tiny_nnz = opt && opt->tiny_max_nnz > 0 ? opt->tiny_max_nnz : kBatchMaxNnz;
+  if (tiny_nnz > (1ll << 22)) tiny_nnz = 1ll << 22;
   std::vector<int32_t> tiny, rest;
   for (int32_t i = 0; i < ngraphs; ++i) {
     const tc_csr_view& v = graphs[i];
     if (!v.offsets || v.nnz < 0 || (v.nnz > 0 && !v.cols))
       return fail(TC_ERR_INVALID_ARG, "tc_count_batch: graph %d has NULL arrays or nnz < 0", i);
-    (v.n <= kBatchMaxN && v.nnz <= kBatchMaxNnz ? tiny : rest).push_back(i);
+    (v.n <= kBatchMaxN && v.nnz <= tiny_nnz ? tiny : rest).push_back(i);
   }
   std::vector<int> st((size_t)ngraphs, TC_OK);
   std::vector<unsigned long long> cnt((size_t)ngraphs, 0ull);
   cudaStream_t user = (cudaStream_t)cuda_stream;
+  // internal stream at the caller's stream priority
+  int prio = 0;
+  if (cudaStreamGetPriority(user, &prio) != cudaSuccess) {
+    cudaGetLastError();
+    prio = 0;
+  }
   cudaStream_t cs = nullptr;
-  TC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  TC_CUDA(cudaStreamCreateWithPriority(&cs, cudaStreamNonBlocking, prio));
   int rc = TC_OK;
   if (!tiny.empty()) rc = run_tiny(graphs, tiny, mode, threads, per_sm, skew, cs, user, cnt, st);
   if (rc == TC_OK && !rest.empty()) rc = run_union(graphs, rest, mode, cs, cnt, st);

@@ -511,22 +511,18 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  const uint32_t* __restrict__ owner_cnt, const uint4* __restrict__ descs,
                  const uint32_t* __restrict__ task_split, const uint32_t* __restrict__ task_idx,
                  uint4* __restrict__ cursors, uint32_t* __restrict__ per_edge,
-                 unsigned long long* item_counter, unsigned long long* ctrl) {
+                 unsigned long long* ctrl) {
   constexpr int kWarps = THREADS / 32;
   constexpr uint32_t kWin = WIN;          // owner entries per table window
   extern __shared__ uint4 tab4[];         // 4 * BUCKETS slots (dynamic shared memory)
-  __shared__ unsigned long long s_item;
   __shared__ unsigned long long s_next;
   uint32_t* tab32 = reinterpret_cast<uint32_t*>(tab4);
   const BucketT* tab = reinterpret_cast<const BucketT*>(tab4);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long acc = 0, probes = 0;
-  while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(item_counter, 1ull);
-    __syncthreads();
-    const unsigned long long it = s_item;
-    __syncthreads();
-    if (it >= nitems) break;
+  // one item per CTA (grid-stride only beyond the grid limit): CTAs end
+  // between items, so work of higher-priority streams gets SMs as they free
+  for (uint64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const uint2 item = items[it];
     const uint32_t o = item.x, slot = item.y >> 16, nsl = item.y & 0xFFFFu;
     const uint64_t T0 = ostart[o], T = owner_cnt[o];
@@ -630,16 +626,15 @@ template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH>
 static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, uint64_t nitems,
                        const unsigned long long* ostart, const uint32_t* owner_cnt,
                        const uint4* descs, const uint32_t* task_split, const uint32_t* task_idx,
-                       uint4* cursors, uint32_t* per_edge, unsigned long long* counter) {
+                       uint4* cursors, uint32_t* per_edge) {
   if (nitems == 0) return TC_OK;
   cudaStream_t st = g->stream;
   const size_t smem = sizeof(uint4) * BUCKETS;
   auto k = k_hash_intersect<M, THREADS, BUCKETS, WIN, MINB, BATCH>;
   TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  TC_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
-  const uint64_t grid = std::min<uint64_t>((uint64_t)sm_count() * MINB, nitems);
+  const uint64_t grid = std::min<uint64_t>(nitems, 0x7FFFFFFFull);
   launch(k, (unsigned)grid, THREADS, smem, st, g->off, g->cols, pcols, items, nitems, ostart,
-         owner_cnt, descs, task_split, task_idx, cursors, per_edge, counter, g->ctrl.p);
+         owner_cnt, descs, task_split, task_idx, cursors, per_edge, g->ctrl.p);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -702,10 +697,10 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   cudaEventRecord(g->ev[6], st);  // end of bucketing
   TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigWin[M], kBigPerSM, false>(
       g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
-      cursors.p, per_edge, counters.p + 2)));
+      cursors.p, per_edge)));
   TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedWin, kMedPerSM, false>(
       g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
-      cursors.p, per_edge, counters.p + 3)));
+      cursors.p, per_edge)));
   cudaEventRecord(g->ev[7], st);  // end of the hash kernels
   // the merge list: small owners (from the count pass) and light owners
   // (appended by the scatter pass); its length is read on the device

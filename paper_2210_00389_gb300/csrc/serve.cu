@@ -13,7 +13,7 @@
 //    from different requests overlaps on the device.
 //  * Every internal wait is bounded (wait_limit_ms): a request that cannot be
 //    admitted in time finishes with TC_ERR_TIMEOUT instead of waiting forever.
-//  * Host-side fault injection for tests: reserved[0] = k > 0 makes the k-th
+//  * Host-side fault injection for tests: fail_admitted = k > 0 makes the k-th
 //    admitted request fail with TC_ERR_OOM as if its allocation had failed.
 //  * Tracing: with TC_SERVE_TRACE=<path> in the environment the server writes
 //    one line per device job (kind B/L/R = batch / large / resident, start
@@ -49,8 +49,9 @@ struct Request {
   uint64_t ticket = 0;
   int mode = TC_MODE_COVER;
   uint64_t graph_id = 0;  // resident graph, or 0 for a one-shot CSR
-  std::vector<int64_t> off;
-  std::vector<uint32_t> cols;
+  std::vector<int64_t> off;   // the request's own copy of a one-shot CSR
+  std::vector<uint32_t> cols;  // (empty when the server borrows views)
+  tc_csr_view view{};          // what the workers count: the copy or the caller's arrays
   uint32_t n = 0;
   size_t est_bytes = 0;
   bool small = false;
@@ -89,14 +90,17 @@ struct tc_server {
   int device = 0;
   std::mutex mu;
   std::condition_variable cv_sched, cv_work;
-  std::deque<std::shared_ptr<Request>> queue;  // submitted, not yet admitted
+  // submitted, not yet admitted: small one-shot requests and the others
+  // (large one-shot and resident), each in arrival order
+  std::deque<std::shared_ptr<Request>> queue_small, queue_large;
   std::deque<std::shared_ptr<Request>> ready_large;
   std::deque<std::shared_ptr<Request>> ready_small;
   std::unordered_map<uint64_t, std::shared_ptr<Request>> tickets;
   std::unordered_map<uint64_t, std::unique_ptr<Resident>> residents;
   size_t resident_bytes = 0;
   size_t inflight_bytes = 0;
-  int inflight = 0;
+  int inflight = 0;        // admitted requests not yet finished
+  int inflight_large = 0;  // of which large one-shot or resident (these take slots)
   uint64_t next_ticket = 1;
   uint64_t next_graph = 1;
   uint64_t admitted = 0;
@@ -126,51 +130,80 @@ struct tc_server {
     r->done = true;
     inflight_bytes -= r->est_bytes;
     --inflight;
+    if (!r->small) --inflight_large;
     cv_sched.notify_all();
   }
 
   // ---------------------------------------------------------------- scheduler
+  // Admit the head of q while `fits` holds; a head that does not fit
+  // blocks its queue (arrival order) and times out after wait_limit.
+  template <class Fits>
+  void admit_from(std::deque<std::shared_ptr<Request>>& q, Fits fits) {
+    while (!q.empty()) {
+      auto r = q.front();
+      if (!fits(*r)) {
+        if (Clock::now() - r->t_submit > wait_limit()) {  // bounded wait for admission
+          q.pop_front();
+          r->status = TC_ERR_TIMEOUT;
+          r->done = true;
+          continue;
+        }
+        return;
+      }
+      q.pop_front();
+      ++inflight;
+      if (!r->small) ++inflight_large;
+      inflight_bytes += r->est_bytes;
+      ++admitted;
+      if (cfg.fail_admitted > 0 && admitted == (uint64_t)cfg.fail_admitted) {
+        // injected allocation failure (host side)
+        --inflight;
+        if (!r->small) --inflight_large;
+        inflight_bytes -= r->est_bytes;
+        r->status = TC_ERR_OOM;
+        r->done = true;
+        continue;
+      }
+      (r->small ? ready_small : ready_large).push_back(r);
+      cv_work.notify_all();
+    }
+  }
+
+  // Small one-shot requests are admitted whenever their bytes fit (they are
+  // batched, and a large request waiting for a slot does not hold them
+  // back); large and resident requests also need one of the `slots`.
   void schedule_loop() {
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
       cv_sched.wait_for(lk, std::chrono::milliseconds(50));
       if (stopping) return;
-      while (!queue.empty()) {
-        auto r = queue.front();
-        const bool fits = inflight < cfg.slots &&
-                          resident_bytes + inflight_bytes + r->est_bytes <= cfg.hbm_budget_bytes;
-        if (!fits) {
-          if (Clock::now() - r->t_submit > wait_limit()) {  // bounded wait for admission
-            queue.pop_front();
-            r->status = TC_ERR_TIMEOUT;
-            r->done = true;
-            continue;
-          }
-          break;
-        }
-        queue.pop_front();
-        ++inflight;
-        inflight_bytes += r->est_bytes;
-        ++admitted;
-        if (cfg.reserved[0] > 0 && admitted == (uint64_t)cfg.reserved[0]) {
-          // injected allocation failure (host side)
-          --inflight;
-          inflight_bytes -= r->est_bytes;
-          r->status = TC_ERR_OOM;
-          r->done = true;
-          continue;
-        }
-        (r->small ? ready_small : ready_large).push_back(r);
-        cv_work.notify_all();
-      }
+      auto bytes_fit = [&](const Request& r) {
+        return resident_bytes + inflight_bytes + r.est_bytes <= cfg.hbm_budget_bytes;
+      };
+      admit_from(queue_small, bytes_fit);
+      admit_from(queue_large,
+                 [&](const Request& r) { return inflight_large < cfg.slots && bytes_fit(r); });
     }
   }
 
   // ---------------------------------------------------------------- workers
+  // Stream priorities: the batch worker's launches (many small requests)
+  // are scheduled ahead of the large ones' CTAs whenever SMs free up.
+  static cudaStream_t make_stream(bool high) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, high ? greatest : least) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    }
+    return s;
+  }
+
   void large_worker() {
     cudaSetDevice(device);
-    cudaStream_t s = nullptr;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaStream_t s = make_stream(false);
     while (true) {
       std::shared_ptr<Request> r;
       {
@@ -199,9 +232,8 @@ struct tc_server {
           st = tc_count(res->g, r->mode, &c);
         }
       } else {
-        tc_csr_view v{r->off.data(), r->cols.data(), r->n, (int64_t)r->cols.size(), 0};
         tc_graph* g = nullptr;
-        st = tc_graph_create(&v, TC_GRAPH_VALIDATE, s, &g);
+        st = tc_graph_create(&r->view, TC_GRAPH_VALIDATE, s, &g);
         if (st == TC_OK) st = tc_count(g, r->mode, &c);
         tc_graph_destroy(g);
         std::vector<int64_t>().swap(r->off);
@@ -216,8 +248,7 @@ struct tc_server {
 
   void batch_worker() {
     cudaSetDevice(device);
-    cudaStream_t s = nullptr;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaStream_t s = make_stream(true);
     while (true) {
       std::vector<std::shared_ptr<Request>> group;
       {
@@ -240,8 +271,7 @@ struct tc_server {
       const auto ta = Clock::now();
       std::vector<tc_csr_view> views(group.size());
       for (size_t i = 0; i < group.size(); ++i)
-        views[i] = tc_csr_view{group[i]->off.data(), group[i]->cols.data(), group[i]->n,
-                               (int64_t)group[i]->cols.size(), 0};
+        views[i] = group[i]->view;
       std::vector<uint64_t> counts(group.size(), 0);
       std::vector<int> status(group.size(), TC_OK);
       const int rc = tc_count_batch(views.data(), (int32_t)views.size(), group[0]->mode, nullptr,
@@ -317,23 +347,28 @@ int tc_serve_submit(tc_server* s, const tc_csr_view* csr_or_null, uint64_t graph
     const tc_csr_view& v = *csr_or_null;
     if (!v.offsets || v.nnz < 0 || (v.nnz > 0 && !v.cols))
       return fail(TC_ERR_INVALID_ARG, "tc_serve_submit: NULL arrays or nnz < 0");
-    // the request keeps its own host copy, so the caller's buffers are free
-    // as soon as this returns
-    r->off.resize((size_t)v.n + 1);
-    r->cols.resize((size_t)v.nnz);
-    if (is_device_ptr(v.offsets)) {
-      TC_CUDA(cudaMemcpy(r->off.data(), v.offsets, sizeof(int64_t) * r->off.size(),
-                         cudaMemcpyDeviceToHost));
+    if (s->cfg.borrow_views) {
+      r->view = v;  // the caller keeps the arrays until the request is done
     } else {
-      memcpy(r->off.data(), v.offsets, sizeof(int64_t) * r->off.size());
-    }
-    if (v.nnz > 0) {
-      if (is_device_ptr(v.cols)) {
-        TC_CUDA(cudaMemcpy(r->cols.data(), v.cols, sizeof(uint32_t) * r->cols.size(),
+      // the request keeps its own host copy, so the caller's buffers are free
+      // as soon as this returns
+      r->off.resize((size_t)v.n + 1);
+      r->cols.resize((size_t)v.nnz);
+      if (is_device_ptr(v.offsets)) {
+        TC_CUDA(cudaMemcpy(r->off.data(), v.offsets, sizeof(int64_t) * r->off.size(),
                            cudaMemcpyDeviceToHost));
       } else {
-        memcpy(r->cols.data(), v.cols, sizeof(uint32_t) * r->cols.size());
+        memcpy(r->off.data(), v.offsets, sizeof(int64_t) * r->off.size());
       }
+      if (v.nnz > 0) {
+        if (is_device_ptr(v.cols)) {
+          TC_CUDA(cudaMemcpy(r->cols.data(), v.cols, sizeof(uint32_t) * r->cols.size(),
+                             cudaMemcpyDeviceToHost));
+        } else {
+          memcpy(r->cols.data(), v.cols, sizeof(uint32_t) * r->cols.size());
+        }
+      }
+      r->view = tc_csr_view{r->off.data(), r->cols.data(), v.n, v.nnz, 0};
     }
     r->n = v.n;
     r->small = v.n <= kServeSmallN && v.nnz <= kServeSmallNnz;
@@ -353,12 +388,12 @@ int tc_serve_submit(tc_server* s, const tc_csr_view* csr_or_null, uint64_t graph
   if (r->est_bytes + s->resident_bytes > s->cfg.hbm_budget_bytes)
     return fail(TC_ERR_OOM, "tc_serve_submit: request needs ~%zu bytes, above the budget",
                 r->est_bytes);
-  if ((int32_t)s->queue.size() >= s->cfg.queue_capacity)
+  if ((int32_t)(s->queue_small.size() + s->queue_large.size()) >= s->cfg.queue_capacity)
     return fail(TC_ERR_AGAIN, "tc_serve_submit: queue full");
   r->ticket = s->next_ticket++;
   r->t_submit = Clock::now();
   s->tickets[r->ticket] = r;
-  s->queue.push_back(r);
+  (r->small ? s->queue_small : s->queue_large).push_back(r);
   *ticket = r->ticket;
   s->cv_sched.notify_all();
   return TC_OK;
@@ -385,12 +420,7 @@ int tc_serve_destroy(tc_server* s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stopping = true;
-    for (auto& r : s->queue) {
-      r->status = TC_ERR_CANCELLED;
-      r->done = true;
-    }
-    s->queue.clear();
-    for (auto* q : {&s->ready_small, &s->ready_large})
+    for (auto* q : {&s->queue_small, &s->queue_large, &s->ready_small, &s->ready_large})
       for (auto& r : *q) {
         r->status = TC_ERR_CANCELLED;
         r->done = true;

@@ -122,3 +122,16 @@ def test_batch_union_path(tc):
         counts, status = tc.tc_count_batch(dev, mode)
         assert status.tolist() == want_st
         assert counts.tolist() == want
+
+
+@pytest.mark.parametrize("tiny", [1, 1 << 11, 1 << 17, 1 << 22])
+def test_batch_split_threshold(tc, tiny):
+    """Any split between the per-graph kernel and the union path gives the
+    same exact counts (tiny = 1: nearly everything in the union)."""
+    gs = mixed_graphs()
+    want = [expected(g) for g in gs]
+    for mode in (tc.TC_MODE_COVER, tc.TC_MODE_PLAIN):
+        counts, status = tc.tc_count_batch([(g.offsets, g.cols) for g in gs], mode,
+                                           tc.Options(256, 2, 0, tiny))
+        assert (status == tc.TC_OK).all()
+        assert counts.tolist() == want

@@ -36,12 +36,15 @@ def drain(tc, s, tickets, timeout=120.0):
     return [out[t] for t in tickets]
 
 
-def test_serve_mix_equals_alone(tc):
+@pytest.mark.parametrize("borrow", [False, True])
+def test_serve_mix_equals_alone(tc, borrow):
     resident = gg.rmat(15, 16, seed=81, relabel_seed=82)
     one_shot = pins.random_small_graphs() + [c[0] for c in pins.closed_form_cases()][:12]
     one_shot += [gg.rmat(s, 8, seed=90 + s) for s in (8, 10, 12)]
     one_shot += [gg.rmat(17, 4, seed=95)]  # large one-shot (n > the batch limit)
-    s = tc.tc_serve_create(8 << 30, slots=16, queue_capacity=1024, wait_limit_ms=60000)
+    # borrowed views: the arrays in one_shot stay alive until drained
+    s = tc.tc_serve_create(8 << 30, slots=16, queue_capacity=1024, wait_limit_ms=60000,
+                           borrow_views=borrow)
     try:
         gid = tc.tc_serve_register(s, resident.offsets, resident.cols)
         tickets, want = [], []

@@ -501,7 +501,8 @@ def run_batch(args, world, rank, local):
                                "p=10/(n-1) / K20-K200, seed 3), one batched launch",
                    "graphs": len(gs), "num_edges": int(units), "triangles": int(outs_b[0].sum()),
                    "options": ({"block_threads": opt.block_threads,
-                                "blocks_per_sm": opt.blocks_per_sm, "skew": opt.skew}
+                                "blocks_per_sm": opt.blocks_per_sm, "skew": opt.skew,
+                                "tiny_max_nnz": opt.tiny_max_nnz, "source": "autotune.json"}
                                if opt else "built-in")},
         "looped_plain": {"value": units / (ms_l / 1e3), "unit": "edges/s", "ms_per_step": ms_l,
                          "batched_speedup": ms_l / ms_b},

@@ -386,25 +386,46 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 
 constexpr int kUnroll = 4;  // probe loads in flight per lane
 
-// All probe elements of a descriptor (runs [0, x) and [cut, end) of P,
-// taken as one index space of x + end - cut elements), kUnroll loads per
-// lane issued before their lookups.
+constexpr uint32_t kGroup = 32 * kUnroll;  // probe elements a warp looks up at once
+
+// A full group: P[lane + 32 j], j < kUnroll, all present, so no bounds or
+// validity tests are executed.
+__device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict__ P,
+                                                     const BucketT* tab, uint32_t nb) {
+  const int lane = threadIdx.x & 31;
+  uint32_t w[kUnroll];
+  bool ok[kUnroll];
+#pragma unroll
+  for (int j = 0; j < kUnroll; ++j) {
+    w[j] = __ldg(P + j * 32 + lane);
+    ok[j] = true;
+  }
+  return table_find_n<kUnroll>(tab, nb, w, ok);
+}
+
+// All probe elements of a descriptor: runs [0, x) and [cut, end) of P.  The
+// full groups of each run are looked up without per-element tests; the two
+// runs' remainders are then taken together as one index space.
 __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
                                               const BucketT* tab, uint32_t nb) {
   const int lane = threadIdx.x & 31;
-  const uint32_t x = ds.y, shift2 = ds.z - ds.y;  // element k >= x sits at P[k + cut - x]
-  const uint32_t total = ds.y + (ds.w - ds.z);
+  const uint32_t x = ds.y, cut = ds.z, n2 = ds.w - ds.z;
+  const uint32_t f1 = x - x % kGroup, f2 = n2 - n2 % kGroup;
   unsigned c = 0;
-  for (uint32_t k0 = 0; k0 < total; k0 += 32 * kUnroll) {
+  for (uint32_t k = 0; k < f1; k += kGroup) c += probe_group_full(P + k, tab, nb);
+  for (uint32_t k = 0; k < f2; k += kGroup) c += probe_group_full(P + cut + k, tab, nb);
+  const uint32_t t1 = x - f1, tt = t1 + (n2 - f2);
+  const uint32_t* P1 = P + f1;
+  const uint32_t* P2 = P + cut + f2 - t1;  // element k >= t1 of the remainder is P2[k]
+  for (uint32_t k0 = 0; k0 < tt; k0 += kGroup) {
     uint32_t w[kUnroll];
+    bool ok[kUnroll];
 #pragma unroll
     for (int j = 0; j < kUnroll; ++j) {
       const uint32_t k = k0 + j * 32 + lane;
-      w[j] = k < total ? __ldg(P + (k < x ? k : k + shift2)) : kEmpty;
+      ok[j] = k < tt;
+      w[j] = ok[j] ? __ldg((k < t1 ? P1 : P2) + k) : kEmpty;
     }
-    bool ok[kUnroll];
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j) ok[j] = w[j] != kEmpty;
     c += table_find_n<kUnroll>(tab, nb, w, ok);
   }
   return c;

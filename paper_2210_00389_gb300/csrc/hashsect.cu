@@ -403,6 +403,25 @@ __device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict_
   return table_find_n<kUnroll>(tab, nb, w, ok);
 }
 
+// U rounds of the remainder index space [0, tt) from k0: element k is
+// P1[k] below t1, else P2[k].
+template <int U>
+__device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ P1,
+                                               const uint32_t* __restrict__ P2, uint32_t t1,
+                                               uint32_t tt, uint32_t k0, const BucketT* tab,
+                                               uint32_t nb) {
+  const int lane = threadIdx.x & 31;
+  uint32_t w[U];
+  bool ok[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const uint32_t k = k0 + j * 32 + lane;
+    ok[j] = k < tt;
+    w[j] = ok[j] ? __ldg((k < t1 ? P1 : P2) + k) : kEmpty;
+  }
+  return table_find_n<U>(tab, nb, w, ok);
+}
+
 // All probe elements of a descriptor: runs [0, x) and [cut, end) of P.  The
 // full groups of each run are looked up without per-element tests; the two
 // runs' remainders are then taken together as one index space.
@@ -417,17 +436,13 @@ __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, ui
   const uint32_t t1 = x - f1, tt = t1 + (n2 - f2);
   const uint32_t* P1 = P + f1;
   const uint32_t* P2 = P + cut + f2 - t1;  // element k >= t1 of the remainder is P2[k]
-  for (uint32_t k0 = 0; k0 < tt; k0 += kGroup) {
-    uint32_t w[kUnroll];
-    bool ok[kUnroll];
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j) {
-      const uint32_t k = k0 + j * 32 + lane;
-      ok[j] = k < tt;
-      w[j] = ok[j] ? __ldg((k < t1 ? P1 : P2) + k) : kEmpty;
-    }
-    c += table_find_n<kUnroll>(tab, nb, w, ok);
-  }
+  // the remainder (< 2 groups): groups of kUnroll rounds while more than two
+  // rounds are left, then one or two rounds, so a short remainder does not
+  // pay for a whole group
+  uint32_t k0 = 0;
+  for (; k0 + 64 < tt; k0 += kGroup) c += probe_tail<kUnroll>(P1, P2, t1, tt, k0, tab, nb);
+  if (k0 + 32 < tt) c += probe_tail<2>(P1, P2, t1, tt, k0, tab, nb);
+  else if (k0 < tt) c += probe_tail<1>(P1, P2, t1, tt, k0, tab, nb);
   return c;
 }
 
@@ -640,6 +655,11 @@ constexpr int kBigThreads = 1024, kBigBuckets = 14336, kBigPerSM = 1;
 // lookups overflowing into a second bucket) can pay.  Tuned on R-MAT scale
 // 20 and 22.
 constexpr int kMedWin = kMedBuckets;
+// Medium owners' edges with fewer than kBatchMaxWork lookups share warp
+// passes (probe_batch) in plain mode, whose upper-neighbour probe lists are
+// often that short; cover probe lists rarely are.  Measured on R-MAT scale
+// 20 and 22.
+constexpr bool kMedBatch[2] = {false, true};
 constexpr int kBigWin[2] = {14336, 28672};
 static_assert(kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
 
@@ -719,7 +739,7 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigWin[M], kBigPerSM, false>(
       g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge)));
-  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedWin, kMedPerSM, false>(
+  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedWin, kMedPerSM, kMedBatch[M]>(
       g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge)));
   cudaEventRecord(g->ev[7], st);  // end of the hash kernels

@@ -404,12 +404,13 @@ __device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict_
 }
 
 // U rounds of the remainder index space [0, tt) from k0: element k is
-// P1[k] below t1, else P2[k].
+// R0[k] below s1, R1[k] below s2, else R2[k] (R1, R2 pre-offset).
 template <int U>
-__device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ P1,
-                                               const uint32_t* __restrict__ P2, uint32_t t1,
-                                               uint32_t tt, uint32_t k0, const BucketT* tab,
-                                               uint32_t nb) {
+__device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ R0,
+                                               const uint32_t* __restrict__ R1,
+                                               const uint32_t* __restrict__ R2, uint32_t s1,
+                                               uint32_t s2, uint32_t tt, uint32_t k0,
+                                               const BucketT* tab, uint32_t nb) {
   const int lane = threadIdx.x & 31;
   uint32_t w[U];
   bool ok[U];
@@ -417,33 +418,62 @@ __device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ P1,
   for (int j = 0; j < U; ++j) {
     const uint32_t k = k0 + j * 32 + lane;
     ok[j] = k < tt;
-    w[j] = ok[j] ? __ldg((k < t1 ? P1 : P2) + k) : kEmpty;
+    w[j] = ok[j] ? __ldg((k < s1 ? R0 : (k < s2 ? R1 : R2)) + k) : kEmpty;
   }
   return table_find_n<U>(tab, nb, w, ok);
 }
 
-// All probe elements of a descriptor: runs [0, x) and [cut, end) of P.  The
-// full groups of each run are looked up without per-element tests; the two
-// runs' remainders are then taken together as one index space.
+// Look up every element of up to three ranges Q[i][0, m[i]): the full
+// groups of each range without per-element tests, then the ranges'
+// remainders together as one index space, in groups of kUnroll rounds
+// while more than two rounds are left, then one or two rounds (a short
+// remainder does not pay for a whole group).
+__device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0,
+                                                 const uint32_t* Q1, uint32_t m1,
+                                                 const uint32_t* Q2, uint32_t m2,
+                                                 const BucketT* tab, uint32_t nb) {
+  const uint32_t f0 = m0 - m0 % kGroup, f1 = m1 - m1 % kGroup, f2 = m2 - m2 % kGroup;
+  unsigned c = 0;
+  for (uint32_t k = 0; k < f0; k += kGroup) c += probe_group_full(Q0 + k, tab, nb);
+  for (uint32_t k = 0; k < f1; k += kGroup) c += probe_group_full(Q1 + k, tab, nb);
+  for (uint32_t k = 0; k < f2; k += kGroup) c += probe_group_full(Q2 + k, tab, nb);
+  const uint32_t r0 = m0 - f0, s1 = r0 + (m1 - f1), tt = s1 + (m2 - f2);
+  const uint32_t* R0 = Q0 + f0;
+  const uint32_t* R1 = Q1 + f1 - r0;
+  const uint32_t* R2 = Q2 + f2 - s1;
+  uint32_t k0 = 0;
+  for (; k0 + 64 < tt; k0 += kGroup)
+    c += probe_tail<kUnroll>(R0, R1, R2, r0, s1, tt, k0, tab, nb);
+  if (k0 + 32 < tt) c += probe_tail<2>(R0, R1, R2, r0, s1, tt, k0, tab, nb);
+  else if (k0 < tt) c += probe_tail<1>(R0, R1, R2, r0, s1, tt, k0, tab, nb);
+  return c;
+}
+
+// All probe elements of a descriptor: runs [0, x) and [cut, end) of P.
 __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
                                               const BucketT* tab, uint32_t nb) {
+  return probe_ranges(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nb);
+}
+
+// Number of elements <= hi in the sorted run P[a, b), by a 32-ary search
+// with warp ballots: one load per lane per round (a run of at most 32
+// elements takes one round, of at most 1,024 two).
+__device__ __forceinline__ uint32_t count_le(const uint32_t* __restrict__ P, uint32_t a,
+                                             uint32_t b, uint32_t hi) {
   const int lane = threadIdx.x & 31;
-  const uint32_t x = ds.y, cut = ds.z, n2 = ds.w - ds.z;
-  const uint32_t f1 = x - x % kGroup, f2 = n2 - n2 % kGroup;
-  unsigned c = 0;
-  for (uint32_t k = 0; k < f1; k += kGroup) c += probe_group_full(P + k, tab, nb);
-  for (uint32_t k = 0; k < f2; k += kGroup) c += probe_group_full(P + cut + k, tab, nb);
-  const uint32_t t1 = x - f1, tt = t1 + (n2 - f2);
-  const uint32_t* P1 = P + f1;
-  const uint32_t* P2 = P + cut + f2 - t1;  // element k >= t1 of the remainder is P2[k]
-  // the remainder (< 2 groups): groups of kUnroll rounds while more than two
-  // rounds are left, then one or two rounds, so a short remainder does not
-  // pay for a whole group
-  uint32_t k0 = 0;
-  for (; k0 + 64 < tt; k0 += kGroup) c += probe_tail<kUnroll>(P1, P2, t1, tt, k0, tab, nb);
-  if (k0 + 32 < tt) c += probe_tail<2>(P1, P2, t1, tt, k0, tab, nb);
-  else if (k0 < tt) c += probe_tail<1>(P1, P2, t1, tt, k0, tab, nb);
-  return c;
+  uint32_t lo = a, n = b - a;
+  while (n > 32) {
+    const uint32_t step = (n + 31) / 32;
+    // lane i samples the last element of block i (clamped to the run)
+    const uint32_t e = min(n, (uint32_t)(lane + 1) * step);
+    const unsigned below = __ballot_sync(0xFFFFFFFFu, __ldg(P + lo + e - 1) <= hi);
+    const uint32_t k = (uint32_t)__popc(below);  // blocks wholly <= hi (a prefix: sorted)
+    if (k == 32) return lo + n - a;
+    lo += k * step;  // the boundary lies in block k
+    n = min(step, n - k * step);
+  }
+  const bool in = (uint32_t)lane < n && __ldg(P + lo + lane) <= hi;
+  return lo - a + (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in));
 }
 
 constexpr uint32_t kBatchMaxWork = 64;  // tasks with fewer lookups share a warp pass
@@ -507,34 +537,6 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
     dj.w = __shfl_sync(0xFFFFFFFFu, ds.w, j);
     c += probe_all(pcols + dj.x, dj, tab, nb);
     if (lane == 0) *probes += desc_work(dj);
-  }
-  return c;
-}
-
-// Look up P[pos..end) while the elements are <= hi (a sorted run); returns
-// the lane's hits and advances pos past the elements looked up.
-__device__ __forceinline__ unsigned probe_run_window(const uint32_t* __restrict__ P, uint32_t& pos,
-                                                     uint32_t end, uint32_t hi,
-                                                     const BucketT* tab, uint32_t nb) {
-  const int lane = threadIdx.x & 31;
-  unsigned c = 0;
-  while (pos < end) {
-    uint32_t w[kUnroll];
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j) {
-      const uint32_t k = pos + j * 32 + lane;
-      w[j] = k < end ? __ldg(P + k) : kEmpty;
-    }
-    uint32_t nin = 0;
-    bool in[kUnroll];
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j) {
-      in[j] = w[j] <= hi;  // kEmpty > hi: padding never counts
-      nin += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in[j]));
-    }
-    c += table_find_n<kUnroll>(tab, nb, w, in);
-    pos += nin;  // the elements <= hi form a prefix of the sorted run
-    if (nin < 32 * kUnroll) break;
   }
   return c;
 }
@@ -608,13 +610,14 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
           const uint32_t z = task_split[t];
           uint4 cur = wdx == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
-          const uint32_t p0 = cur.x, p1 = cur.y, p2 = cur.z;
-          c = probe_run_window(P, cur.x, ds.y, hi, tab, nb);
-          c += probe_run_window(P, cur.y, z, hi, tab, nb);
-          c += probe_run_window(P, cur.z, ds.w, hi, tab, nb);
+          // this window's elements of each run: the prefix <= hi
+          const uint32_t m0 = count_le(P, cur.x, ds.y, hi);
+          const uint32_t m1 = count_le(P, cur.y, z, hi);
+          const uint32_t m2 = count_le(P, cur.z, ds.w, hi);
+          c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, nb);
           if (lane == 0) {
-            probes += (cur.x - p0) + (cur.y - p1) + (cur.z - p2);
-            if (wdx + 1 < nwin) cursors[t] = cur;
+            probes += m0 + m1 + m2;
+            if (wdx + 1 < nwin) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
           }
         }
         acc += c;

@@ -85,10 +85,12 @@ def make_graph(workload: str, rank: int):
     elif workload == "rmat10":
         g = gg.rmat(10, 16, 1 + rank * 1000)
         desc = "R-MAT scale 10, edgefactor 16, seed 1"
-    else:
+    elif workload == "chunglu23":
         g = gg.chung_lu_islands(1 << 23, seed=7 + rank * 1000)
         desc = ("Chung-Lu n=2^23, gamma 2.1, mean degree 32, cap 65536, "
                 "10% Erdos-Renyi islands of 16-256 vertices, seed 7")
+    else:
+        raise ValueError(f"{workload} is not a single-graph workload")
     return g, desc
 
 
@@ -267,8 +269,59 @@ def barrier(world):
         dist.barrier()
 
 
+def oracle_graph_sample(gs, target_s: float, seed: int = 0):
+    """Time the CPU oracle (Alg. 1: BFS, cover edges, count) graph by graph
+    on a uniform random sample of the list gs, for about target_s seconds.
+    Returns (edges per second, description)."""
+    import random
+    import oracle
+    order = list(range(len(gs)))
+    random.Random(seed).shuffle(order)
+    edges, t0 = 0, time.perf_counter()
+    done = 0
+    for i in order:
+        oracle.cetc(gs[i])
+        edges += gs[i].num_edges
+        done += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    dt = time.perf_counter() - t0
+    return edges / dt, (f"oracle BFS + cover edges + count-once intersection, one graph at a "
+                        f"time, on {done} of {len(gs)} graphs drawn uniformly ({dt:.2f} s); "
+                        f"single thread")
+
+
 def run_reference(args, world, rank):
     if rank != 0:
+        return
+    if args.workload in ("batch", "serve"):
+        # the oracle over a sample of the workload's graphs, one at a time
+        import graphgen as gg
+        specs = gg.mixed_graph_specs(4096, seed=3 if args.workload == "batch" else 11)
+        gs = [gg.graph_from_spec(sp) for sp in specs[:512]]
+        rates, sample_desc = [], ""
+        for i in range(args.warmup + args.steps):
+            r, sample_desc = oracle_graph_sample(gs, target_s=2.0, seed=i)
+            if i >= args.warmup:
+                rates.append(r)
+        value = statistics.mean(rates)
+        desc = ("mixed graphs (R-MAT s6-14 ef8-32 / ER n256-4096 p=10/(n-1) / K20-K200), "
+                f"seed {3 if args.workload == 'batch' else 11}; the oracle counts them one at "
+                "a time")
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            # one step = the 4,096 graphs, estimated from the sampled rate
+            "ms_per_step": 1e3 * 4096 * statistics.mean(g.num_edges for g in gs) / value,
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": desc},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": sample_desc, **cpu_info()},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
         return
     g, desc = make_graph(args.workload, 0)
     times = []

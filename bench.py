@@ -51,7 +51,9 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
                     choices=["rmat22", "rmat10", "rmat18", "rmat20", "rmat26", "chunglu23",
-                             "batch", "serve"])
+                             "batch", "serve", "kstudy"])
+    ap.add_argument("--kstudy-max-scale", type=int, default=24,
+                    help="kstudy: largest R-MAT scale (from 6)")
     ap.add_argument("--requests", type=int, default=20000, help="serve: stream length")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
     ap.add_argument("--serve-scale", type=int, default=26, help="serve: resident R-MAT scale")
@@ -720,6 +722,54 @@ def run_serve(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_kstudy(args, world, rank):
+    """The cover-edge fraction k = |H| / |E| of R-MAT graphs against the scale
+    on the GPU, with the max-degree root rule and with one uniformly random
+    root (the rest rooted at their lowest id), next to the paper's fit
+    k = 1.1773 e^(-0.036 scale) (Sec. IV-A), and the Comm-CETC communication
+    model (Sec. III-B) evaluated with the measured k and levels against the
+    wedge-checking volume from the exact wedge count, for p = 128.  One JSON
+    line; not a benchmark metric."""
+    import random
+
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2210_00389_gb300 as tc
+    from paper_2210_00389_gb300 import comm
+
+    if rank != 0:
+        return
+    dev = torch.device("cuda", 0)
+    rows = []
+    for scale in range(6, args.kstudy_max_scale + 1):
+        g = gg.rmat(scale, 16, seed=scale, relabel_seed=scale + 2 ** 32)
+        off = torch.from_numpy(g.offsets).to(dev)
+        cols = torch.from_numpy(g.cols).to(dev)
+        deg = np.diff(g.offsets)
+        with tc.Graph(off, cols, n=g.n, flags=tc.TC_GRAPH_BORROW) as G:
+            _, nl = G.levels()
+            h_max = G.cover_edge_count()
+            r = random.Random(scale).choice(np.flatnonzero(deg > 0).tolist())
+            _, nl_r = G.levels([r])
+            h_rand = G.cover_edge_count()
+        m = g.num_edges
+        wedges = int((deg.astype(np.int64) * (deg.astype(np.int64) - 1) // 2).sum())
+        log_d = comm.clog2(max(nl, 2))
+        ours = comm.comm_cetc_bits(g.n, m, h_max / m, 128, log_d) / 8
+        prev = comm.wedge_check_bits(wedges, g.n) / 8
+        rows.append({"scale": scale, "n": g.n, "edges": m, "levels": nl,
+                     "k_max_degree_root": h_max / m, "k_random_root": h_rand / m,
+                     "levels_random_root": nl_r, "k_fit": comm.k_fit(scale),
+                     "wedges": wedges, "comm_cetc_bytes_p128": ours,
+                     "wedge_check_bytes": prev, "reduction_p128": prev / ours})
+        del off, cols
+    print(json.dumps({"study": "cover-edge fraction k vs R-MAT scale (edgefactor 16, "
+                               "relabelled, seed = scale)",
+                      "fit": "k = 1.1773 exp(-0.036 scale)", "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_init()
@@ -727,6 +777,8 @@ def main():
         run_serve(args, world, rank, local)
     elif args.workload == "batch" and args.impl == "ours":
         run_batch(args, world, rank, local)
+    elif args.workload == "kstudy":
+        run_kstudy(args, world, rank)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

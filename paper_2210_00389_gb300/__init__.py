@@ -260,6 +260,14 @@ def tc_bfs_levels(g: int, roots=None, out=None):
     return out, nl.value
 
 
+def tc_cover_edge_count(g: int) -> int:
+    """|H| (Thm. 1) without copying the cover edges out (tc_cover_edges with
+    uv_out = NULL)."""
+    cnt = ctypes.c_int64(0)
+    _check(_lib.tc_cover_edges(g, None, 0, ctypes.byref(cnt)), "tc_cover_edges")
+    return cnt.value
+
+
 def tc_cover_edges(g: int, out=None):
     """Cover-edge set H (Thm. 1) as a (|H|, 2) uint32 array (or into `out`)."""
     cnt = ctypes.c_int64(0)
@@ -433,6 +441,9 @@ class Graph:
 
     def cover_edges(self, out=None):
         return tc_cover_edges(self.handle, out)
+
+    def cover_edge_count(self) -> int:
+        return tc_cover_edge_count(self.handle)
 
     def cover_edge_counts(self, out=None):
         return tc_cover_edge_counts(self.handle, out)

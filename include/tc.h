@@ -164,6 +164,22 @@ TC_API int tc_count(tc_graph* g, int mode, uint64_t* count_out);
  * counts_out: host/device uint32[cap].  TC_ERR_CAPACITY if |H| > cap. */
 TC_API int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap);
 
+/* Triangle finding (the cover edges' second use, Alg. 1 / Thm. 2): every
+ * triangle is found once, at the cover edge (u, v), u < v, that the
+ * count-once rule attributes it to, with apex w.
+ *
+ * tc_vertex_counts: counts_out (host or device uint64[n]) receives, for
+ * every vertex, the number of triangles that contain it (sum = 3T).
+ *
+ * tc_list_triangles: tri_out (host or device uint32[3 * cap], or NULL to only
+ * count) receives the T triangles as triples (u, v, w) in no particular
+ * order; *count_out = T.  If T > cap and tri_out != NULL, nothing is written
+ * and TC_ERR_CAPACITY is returned (with *count_out set).
+ * Both run the BFS and the cover extraction first if they are not cached.
+ * Errors: TC_ERR_INVALID_ARG, TC_ERR_CAPACITY, TC_ERR_OOM, TC_ERR_CUDA. */
+TC_API int tc_vertex_counts(tc_graph* g, uint64_t* counts_out);
+TC_API int tc_list_triangles(tc_graph* g, uint32_t* tri_out, int64_t cap, int64_t* count_out);
+
 /* Shards of the count for several GPUs (the CSR and the levels replicated on
  * each; every GPU counts one contiguous slice; the slice counts add up to T).
  * The count is a sum of independent per-edge terms over the mode's edge

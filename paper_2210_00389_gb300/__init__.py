@@ -106,6 +106,8 @@ _SIGS = {
     "tc_count": (ctypes.c_int, [_vp, ctypes.c_int, _u64p]),
     "tc_cover_edge_counts": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
     "tc_shard_bounds": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int32, _vp]),
+    "tc_vertex_counts": (ctypes.c_int, [_vp, _vp]),
+    "tc_list_triangles": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _i64p]),
     "tc_count_range": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _u64p]),
     "tc_count_plain_static": (ctypes.c_int, [_vp, _vp, ctypes.c_uint32, ctypes.c_int64, _vp, _vp]),
     "tc_count_batch": (ctypes.c_int, [ctypes.POINTER(CSRView), ctypes.c_int32, ctypes.c_int,
@@ -286,6 +288,28 @@ def tc_count(g: int, mode: int = TC_MODE_COVER) -> int:
     return c.value
 
 
+def tc_vertex_counts(g: int, out=None):
+    """uint64[n]: triangles containing each vertex (host numpy, or into a
+    given numpy array / CUDA tensor)."""
+    n = tc_graph_info(g)["n"]
+    if out is None:
+        out = np.zeros(n, dtype=np.uint64)
+    op, _ = _ptr(out)
+    _check(_lib.tc_vertex_counts(g, op if n else None), "tc_vertex_counts")
+    return out
+
+
+def tc_list_triangles(g: int) -> np.ndarray:
+    """(T, 3) uint32 array of the triangles as (u, v, w): (u, v) the cover
+    edge the count-once rule attributes the triangle to, w the apex."""
+    cnt = ctypes.c_int64(0)
+    _check(_lib.tc_list_triangles(g, None, 0, ctypes.byref(cnt)), "tc_list_triangles")
+    out = np.empty((max(cnt.value, 1), 3), dtype=np.uint32)
+    _check(_lib.tc_list_triangles(g, out.ctypes.data, cnt.value, ctypes.byref(cnt)),
+           "tc_list_triangles")
+    return out[:cnt.value]
+
+
 def tc_shard_bounds(g: int, mode: int, nshards: int) -> np.ndarray:
     """int64[nshards + 1] work-balanced bounds of the mode's edge index space."""
     b = np.zeros(nshards + 1, dtype=np.int64)
@@ -432,6 +456,12 @@ class Graph:
 
     def levels(self, roots=None, out=None):
         return tc_bfs_levels(self.handle, roots, out)
+
+    def vertex_counts(self, out=None):
+        return tc_vertex_counts(self.handle, out)
+
+    def list_triangles(self) -> np.ndarray:
+        return tc_list_triangles(self.handle)
 
     def shard_bounds(self, mode: int, nshards: int) -> np.ndarray:
         return tc_shard_bounds(self.handle, mode, nshards)

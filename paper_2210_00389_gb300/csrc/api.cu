@@ -106,6 +106,54 @@ int tc_count(tc_graph* g, int mode, uint64_t* count_out) {
   return TC_OK;
 }
 
+int tc_vertex_counts(tc_graph* g, uint64_t* counts_out) {
+  if (!g || (!counts_out && g->n > 0))
+    return fail(TC_ERR_INVALID_ARG, "tc_vertex_counts: NULL argument");
+  DeviceGuard dg(g->device);
+  if (g->n == 0) return TC_OK;
+  if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
+  if (g->num_cover < 0) TC_TRY(compute_cover(g));
+  DevBuf<unsigned long long> tv;
+  TC_TRY(tv.alloc(g->n, g->stream));
+  TC_TRY(find_vertex_counts(g, tv.p));
+  TC_CUDA(copy_out(counts_out, tv.p, sizeof(uint64_t) * g->n, g->stream));
+  TC_CUDA(cudaStreamSynchronize(g->stream));
+  return TC_OK;
+}
+
+int tc_list_triangles(tc_graph* g, uint32_t* tri_out, int64_t cap, int64_t* count_out) {
+  if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_list_triangles: NULL argument");
+  if (tri_out && cap < 0) return fail(TC_ERR_INVALID_ARG, "tc_list_triangles: cap < 0");
+  DeviceGuard dg(g->device);
+  if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
+  if (g->num_cover < 0) TC_TRY(compute_cover(g));
+  // T first (the hashed count), so the list is written only when it fits
+  uint64_t T = 0;
+  TC_TRY(count_cover(g, nullptr, &T));
+  *count_out = (int64_t)T;
+  if (!tri_out || T == 0) return TC_OK;
+  if ((int64_t)T > cap)
+    return fail(TC_ERR_CAPACITY, "tc_list_triangles: T = %llu > cap = %lld",
+                (unsigned long long)T, (long long)cap);
+  const bool dev = is_device_ptr(tri_out);
+  DevBuf<uint32_t> tmp;
+  uint32_t* out = tri_out;
+  if (!dev) {
+    TC_TRY(tmp.alloc((size_t)T * 3, g->stream));
+    out = tmp.p;
+  }
+  uint64_t found = 0;
+  TC_TRY(find_list(g, out, T, &found));
+  if (found != T)
+    return fail(TC_ERR_CUDA, "tc_list_triangles: found %llu triangles, counted %llu",
+                (unsigned long long)found, (unsigned long long)T);
+  if (!dev) {
+    TC_CUDA(copy_out(tri_out, out, sizeof(uint32_t) * 3 * (size_t)T, g->stream));
+    TC_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  return TC_OK;
+}
+
 int tc_shard_bounds(tc_graph* g, int mode, int32_t nshards, int64_t* bounds_out) {
   if (!g || !bounds_out) return fail(TC_ERR_INVALID_ARG, "tc_shard_bounds: NULL argument");
   if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)

@@ -188,6 +188,12 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t fi
 int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry = nullptr, int64_t first = 0,
                 int64_t last = -1);
 
+// Triangle finding (find.cu): per-vertex counts into tv_dev (n entries,
+// device), and the list of triangles (u, v, w) into out_dev (3 * cap
+// entries, device; *found = the number of triangles, which may exceed cap).
+int find_vertex_counts(tc_graph* g, unsigned long long* tv_dev);
+int find_list(tc_graph* g, uint32_t* out_dev, unsigned long long cap, uint64_t* found);
+
 // Work-balanced shard bounds of the mode's edge index space (shard.cu):
 // bounds_host[0] = 0 <= ... <= bounds_host[P] = |edges|.
 int shard_bounds(tc_graph* g, int mode, int32_t P, int64_t* bounds_host);

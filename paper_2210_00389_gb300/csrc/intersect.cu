@@ -104,12 +104,31 @@ k_cover_intersect(const uint2* __restrict__ H, int64_t nh, const int64_t* __rest
   block_add(elems, &ctrl[kCtrlElems]);
 }
 
+// |A ∩ B| by one thread: a two-pointer merge of short sorted lists.
+__device__ __forceinline__ unsigned thread_merge(const uint32_t* __restrict__ A, uint32_t la,
+                                                 const uint32_t* __restrict__ B, uint32_t lb) {
+  unsigned c = 0;
+  uint32_t i = 0, j = 0;
+  while (i < la && j < lb) {
+    const uint32_t a = __ldg(A + i), b = __ldg(B + j);
+    c += a == b;
+    i += a <= b;
+    j += b <= a;
+  }
+  return c;
+}
+
+constexpr uint32_t kThreadMerge = 48;  // list elements a single thread merges
+
 // Edges listed by the bucketing step as having a small owner (both
 // endpoints of degree <= the small-owner bound, or an owner whose edges are
-// too few to pay for a hash table): warp merge, list chunks grabbed from
-// *work; the list length is read from device memory (*nlist_dev), since the
-// bucketing step appends to it on the GPU.  mode 0 = cover (list holds H
-// indices), 1 = plain (list holds CSR entry indices with u < v).
+// too few to pay for a hash table).  A warp takes 32 list entries, one per
+// lane: a lane whose lists are short (at most kThreadMerge elements in all)
+// merges them alone; the other entries are then merged by the whole warp,
+// one at a time.  The list length is read from device memory
+// (*nlist_dev), since the bucketing step appends to it on the GPU.
+// mode 0 = cover (list holds H indices), 1 = plain (list holds CSR entry
+// indices with u < v).
 __global__ void __launch_bounds__(kIsThreads)
 k_small_merge(int mode, const uint32_t* __restrict__ list, const unsigned long long* nlist_dev,
               const uint2* __restrict__ H, const int64_t* __restrict__ off,
@@ -122,31 +141,67 @@ k_small_merge(int mode, const uint32_t* __restrict__ list, const unsigned long l
   unsigned long long acc = 0, elems = 0;
   while (true) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(work, (unsigned long long)kPlainChunk);
+    if (lane == 0) base = atomicAdd(work, 32ull);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     if ((int64_t)base >= nlist) break;
-    const int64_t end = min((int64_t)base + kPlainChunk, nlist);
-    for (int64_t j = (int64_t)base; j < end; ++j) {
-      const int64_t i = list[j];
-      unsigned c;
+    const int64_t j = (int64_t)base + lane;
+    int64_t i = -1;
+    bool big = false;
+    if (j < nlist) {
+      i = list[j];
+      unsigned c = 0;
+      uint32_t len = 0;
       if (mode == 0) {
-        c = cover_edge_merge(i, H, off, scols, seg, hoff, &elems);
-        if (per_edge) {
-          const unsigned long long t = warp_sum(c);
-          if (lane == 0) per_edge[i] = (uint32_t)t;
+        const uint2 e = H[i];
+        const int64_t ou = off[e.x], eu = off[e.x + 1];
+        const int64_t ov = off[e.y], ev = off[e.y + 1];
+        const uint4 su = seg[e.x], sv = seg[e.y];
+        // v is entry (i - hoff[u]) of u's same-level run above u
+        const uint32_t cut = su.y + (uint32_t)(i - (int64_t)hoff[e.x]) + 1u;
+        const uint32_t du = (uint32_t)(eu - ou), dv = (uint32_t)(ev - ov);
+        len = su.x + sv.x + (su.z - cut) + (sv.z - sv.y) + (du - su.z) + (dv - sv.z);
+        if (len <= kThreadMerge) {
+          const uint32_t* Ru = scols + ou;
+          const uint32_t* Rv = scols + ov;
+          c = thread_merge(Ru, su.x, Rv, sv.x) +                                // level l-1
+              thread_merge(Ru + cut, su.z - cut, Rv + sv.y, sv.z - sv.y) +     // level l, > v
+              thread_merge(Ru + su.z, du - su.z, Rv + sv.z, dv - sv.z);        // level l+1
         }
       } else {
         const uint32_t u = erow[i], v = cols[i];
         const int64_t au = i + 1, bv = ustart[v];
+        const uint32_t la = (uint32_t)(off[u + 1] - au), lb = (uint32_t)(off[v + 1] - bv);
+        len = la + lb;
+        if (len <= kThreadMerge) c = thread_merge(cols + au, la, cols + bv, lb);
+      }
+      big = len > kThreadMerge;
+      if (!big) {
+        acc += c;
+        elems += len;
+        if (per_edge) per_edge[i] = c;
+      }
+    }
+    // the long ones: the whole warp, one entry at a time
+    unsigned m = __ballot_sync(0xFFFFFFFFu, big);
+    while (m) {
+      const int r = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t ir = __shfl_sync(0xFFFFFFFFu, i, r);
+      unsigned c;
+      if (mode == 0) {
+        c = cover_edge_merge(ir, H, off, scols, seg, hoff, &elems);
+      } else {
+        const uint32_t u = erow[ir], v = cols[ir];
+        const int64_t au = ir + 1, bv = ustart[v];
         const int64_t la = off[u + 1] - au, lb = off[v + 1] - bv;
         c = warp_intersect(cols + au, la, cols + bv, lb);
         if (lane == 0) elems += (unsigned long long)(la + lb);
-        if (per_edge) {
-          const unsigned long long t = warp_sum(c);
-          if (lane == 0) per_edge[i] = (uint32_t)t;
-        }
       }
       acc += c;
+      if (per_edge) {
+        const unsigned long long t = warp_sum(c);
+        if (lane == 0) per_edge[ir] = (uint32_t)t;
+      }
     }
   }
   block_add(acc, &ctrl[kCtrlCount]);

@@ -9,8 +9,10 @@
 // warp-per-cover-edge merge over the level-segmented rows (segments l-1,
 // "same level above v", l+1; see segment.cu), with a sink called on every
 // accepted apex: it adds one to the apex's count, or appends (u, v, w) to
-// the list.  The title's second use of cover edges, finding triangles, is
-// this step.
+// the list.  Per-vertex counts go through the hash intersection of
+// hashsect.cu, with a sink per hit, wherever it applies; this file's merge
+// kernel then takes the small-owner edges (and whole graphs beyond the hash
+// path's 32-bit task lists).
 #include "internal.cuh"
 #include "warp_isect.cuh"
 
@@ -96,6 +98,34 @@ k_find_vertex(const uint2* __restrict__ H, int64_t nh, const int64_t* __restrict
   }
 }
 
+// The same for the cover edges listed in list[0 .. *nlist_dev): the
+// small-owner edges of the hashed path.
+__global__ void __launch_bounds__(kFindThreads)
+k_find_vertex_list(const uint32_t* __restrict__ list, const unsigned long long* nlist_dev,
+                   const uint2* __restrict__ H, const int64_t* __restrict__ off,
+                   const uint32_t* __restrict__ scols, const uint4* __restrict__ seg,
+                   const unsigned long long* __restrict__ hoff, unsigned long long* tv,
+                   unsigned long long* work) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nl = (int64_t)*nlist_dev;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(work, (unsigned long long)kFindChunk);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if ((int64_t)base >= nl) break;
+    const int64_t end = min((int64_t)base + kFindChunk, nl);
+    for (int64_t j = (int64_t)base; j < end; ++j) {
+      const int64_t i = list[j];
+      const unsigned c = find_warp_sum(find_edge(i, H, off, scols, seg, hoff, VertexSink{tv}));
+      if (lane == 0 && c) {
+        const uint2 e = H[i];
+        atomicAdd(&tv[e.x], (unsigned long long)c);
+        atomicAdd(&tv[e.y], (unsigned long long)c);
+      }
+    }
+  }
+}
+
 // Warp per cover edge: every triangle as (u, v, w).
 __global__ void __launch_bounds__(kFindThreads)
 k_find_list(const uint2* __restrict__ H, int64_t nh, const int64_t* __restrict__ off,
@@ -116,10 +146,28 @@ k_find_list(const uint2* __restrict__ H, int64_t nh, const int64_t* __restrict__
   }
 }
 
+int find_vertex_list(tc_graph* g, const uint32_t* list, const unsigned long long* nlist_dev,
+                     uint64_t nlist_max, unsigned long long* tv_dev) {
+  cudaStream_t s = g->stream;
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
+  launch(k_find_vertex_list, grid_for((int64_t)nlist_max * 32, kFindThreads, 8), kFindThreads, 0,
+         s, list, nlist_dev, g->cover.p, g->off, g->scols.p, g->seg.p, g->hoff.p, tv_dev,
+         g->ctrl.p + kCtrlWork);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+// Per-vertex counts: through the hash intersection (a sink per hit) when
+// the edge and entry counts fit its 32-bit task lists, else by the merge.
 int find_vertex_counts(tc_graph* g, unsigned long long* tv_dev) {
   cudaStream_t s = g->stream;
   if (g->num_cover < 0) TC_TRY(compute_cover(g));
   TC_CUDA(cudaMemsetAsync(tv_dev, 0, sizeof(unsigned long long) * (size_t)g->n, s));
+  if (g->num_cover < (int64_t)0xFFFFFFFFll && g->nnz < (int64_t)0xFFFFFFFFll) {
+    TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlCount, 0, sizeof(unsigned long long), s));
+    TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
+    return hash_count(g, 0, nullptr, nullptr, 0, g->num_cover, tv_dev);
+  }
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWork, 0, sizeof(unsigned long long), s));
   if (g->num_cover > 0)
     launch(k_find_vertex, grid_for(g->num_cover * 32, kFindThreads, 8), kFindThreads, 0, s,

@@ -342,10 +342,22 @@ __device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t nb, uint32_
 // padding).  The U first bucket reads are issued together (lanes with an
 // invalid key read nothing); a key whose bucket is full without a match
 // moves to the next bucket, and that loop runs only while some key of some
-// lane still needs one.  Returns the lane's hits.
-template <int U>
+// lane still needs one.  Returns the lane's hits; sink(w) is called on each
+// (NoSink: nothing, for the counts).
+struct NoSink {
+  __device__ __forceinline__ void operator()(uint32_t) const {}
+};
+
+// Per-vertex triangle counts: one for the apex of every hit.
+struct ApexSink {
+  unsigned long long* tv;
+  __device__ __forceinline__ void operator()(uint32_t w) const { atomicAdd(&tv[w], 1ull); }
+};
+
+template <int U, class Sink = NoSink>
 __device__ __forceinline__ unsigned table_find_n(const BucketT* tab, uint32_t nb,
-                                                 const uint32_t (&w)[U], const bool (&valid)[U]) {
+                                                 const uint32_t (&w)[U], const bool (&valid)[U],
+                                                 Sink sink = Sink()) {
   uint32_t b[U];
   BucketT q[U];
 #pragma unroll
@@ -376,6 +388,9 @@ __device__ __forceinline__ unsigned table_find_n(const BucketT* tab, uint32_t nb
   unsigned c = 0;
 #pragma unroll
   for (int j = 0; j < U; ++j) c += hit[j] ? 1u : 0u;
+#pragma unroll
+  for (int j = 0; j < U; ++j)
+    if (hit[j]) sink(w[j]);
   return c;
 }
 
@@ -390,8 +405,10 @@ constexpr uint32_t kGroup = 32 * kUnroll;  // probe elements a warp looks up at 
 
 // A full group: P[lane + 32 j], j < kUnroll, all present, so no bounds or
 // validity tests are executed.
+template <class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict__ P,
-                                                     const BucketT* tab, uint32_t nb) {
+                                                     const BucketT* tab, uint32_t nb,
+                                                     Sink sink = Sink()) {
   const int lane = threadIdx.x & 31;
   uint32_t w[kUnroll];
   bool ok[kUnroll];
@@ -400,17 +417,18 @@ __device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict_
     w[j] = __ldg(P + j * 32 + lane);
     ok[j] = true;
   }
-  return table_find_n<kUnroll>(tab, nb, w, ok);
+  return table_find_n<kUnroll>(tab, nb, w, ok, sink);
 }
 
 // U rounds of the remainder index space [0, tt) from k0: element k is
 // R0[k] below s1, R1[k] below s2, else R2[k] (R1, R2 pre-offset).
-template <int U>
+template <int U, class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ R0,
                                                const uint32_t* __restrict__ R1,
                                                const uint32_t* __restrict__ R2, uint32_t s1,
                                                uint32_t s2, uint32_t tt, uint32_t k0,
-                                               const BucketT* tab, uint32_t nb) {
+                                               const BucketT* tab, uint32_t nb,
+                                               Sink sink = Sink()) {
   const int lane = threadIdx.x & 31;
   uint32_t w[U];
   bool ok[U];
@@ -420,7 +438,7 @@ __device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ R0,
     ok[j] = k < tt;
     w[j] = ok[j] ? __ldg((k < s1 ? R0 : (k < s2 ? R1 : R2)) + k) : kEmpty;
   }
-  return table_find_n<U>(tab, nb, w, ok);
+  return table_find_n<U>(tab, nb, w, ok, sink);
 }
 
 // Look up every element of up to three ranges Q[i][0, m[i]): the full
@@ -428,31 +446,35 @@ __device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ R0,
 // remainders together as one index space, in groups of kUnroll rounds
 // while more than two rounds are left, then one or two rounds (a short
 // remainder does not pay for a whole group).
+template <class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0,
                                                  const uint32_t* Q1, uint32_t m1,
                                                  const uint32_t* Q2, uint32_t m2,
-                                                 const BucketT* tab, uint32_t nb) {
+                                                 const BucketT* tab, uint32_t nb,
+                                                 Sink sink = Sink()) {
   const uint32_t f0 = m0 - m0 % kGroup, f1 = m1 - m1 % kGroup, f2 = m2 - m2 % kGroup;
   unsigned c = 0;
-  for (uint32_t k = 0; k < f0; k += kGroup) c += probe_group_full(Q0 + k, tab, nb);
-  for (uint32_t k = 0; k < f1; k += kGroup) c += probe_group_full(Q1 + k, tab, nb);
-  for (uint32_t k = 0; k < f2; k += kGroup) c += probe_group_full(Q2 + k, tab, nb);
+  for (uint32_t k = 0; k < f0; k += kGroup) c += probe_group_full(Q0 + k, tab, nb, sink);
+  for (uint32_t k = 0; k < f1; k += kGroup) c += probe_group_full(Q1 + k, tab, nb, sink);
+  for (uint32_t k = 0; k < f2; k += kGroup) c += probe_group_full(Q2 + k, tab, nb, sink);
   const uint32_t r0 = m0 - f0, s1 = r0 + (m1 - f1), tt = s1 + (m2 - f2);
   const uint32_t* R0 = Q0 + f0;
   const uint32_t* R1 = Q1 + f1 - r0;
   const uint32_t* R2 = Q2 + f2 - s1;
   uint32_t k0 = 0;
   for (; k0 + 64 < tt; k0 += kGroup)
-    c += probe_tail<kUnroll>(R0, R1, R2, r0, s1, tt, k0, tab, nb);
-  if (k0 + 32 < tt) c += probe_tail<2>(R0, R1, R2, r0, s1, tt, k0, tab, nb);
-  else if (k0 < tt) c += probe_tail<1>(R0, R1, R2, r0, s1, tt, k0, tab, nb);
+    c += probe_tail<kUnroll>(R0, R1, R2, r0, s1, tt, k0, tab, nb, sink);
+  if (k0 + 32 < tt) c += probe_tail<2>(R0, R1, R2, r0, s1, tt, k0, tab, nb, sink);
+  else if (k0 < tt) c += probe_tail<1>(R0, R1, R2, r0, s1, tt, k0, tab, nb, sink);
   return c;
 }
 
 // All probe elements of a descriptor: runs [0, x) and [cut, end) of P.
+template <class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
-                                              const BucketT* tab, uint32_t nb) {
-  return probe_ranges(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nb);
+                                              const BucketT* tab, uint32_t nb,
+                                              Sink sink = Sink()) {
+  return probe_ranges(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nb, sink);
 }
 
 // Number of elements <= hi in the sorted run P[a, b), by a 32-ary search
@@ -541,7 +563,10 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
   return c;
 }
 
-template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH>
+// VERT (cover mode only): per-vertex triangle counts instead of per-edge
+// ones -- every hit adds one to its apex, and each edge's count is added to
+// both of its endpoints (H[task_idx[t]]).
+template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH, bool VERT>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                  const uint32_t* __restrict__ pcols, const uint2* __restrict__ items,
@@ -549,6 +574,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  const uint32_t* __restrict__ owner_cnt, const uint4* __restrict__ descs,
                  const uint32_t* __restrict__ task_split, const uint32_t* __restrict__ task_idx,
                  uint4* __restrict__ cursors, uint32_t* __restrict__ per_edge,
+                 const uint2* __restrict__ H, unsigned long long* __restrict__ tv,
                  unsigned long long* ctrl) {
   constexpr int kWarps = THREADS / 32;
   constexpr uint32_t kWin = WIN;          // owner entries per table window
@@ -604,7 +630,8 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         const uint32_t* P = pcols + ds.x;
         unsigned c;
         if (nwin == 1) {
-          c = probe_all(P, ds, tab, nb);
+          if constexpr (VERT) c = probe_all(P, ds, tab, nb, ApexSink{tv});
+          else c = probe_all(P, ds, tab, nb);
           if (lane == 0) probes += desc_work(ds);
         } else {
           // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
@@ -614,7 +641,10 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           const uint32_t m0 = count_le(P, cur.x, ds.y, hi);
           const uint32_t m1 = count_le(P, cur.y, z, hi);
           const uint32_t m2 = count_le(P, cur.z, ds.w, hi);
-          c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, nb);
+          if constexpr (VERT)
+            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, nb, ApexSink{tv});
+          else
+            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, nb);
           if (lane == 0) {
             probes += m0 + m1 + m2;
             if (wdx + 1 < nwin) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
@@ -624,6 +654,14 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         if (per_edge) {
           const unsigned long long tsum = warp_sum_u64(c);
           if (lane == 0 && tsum) atomicAdd(&per_edge[task_idx[t]], (uint32_t)tsum);
+        }
+        if constexpr (VERT) {
+          const unsigned long long tsum = warp_sum_u64(c);
+          if (lane == 0 && tsum) {
+            const uint2 e = H[task_idx[t]];
+            atomicAdd(&tv[e.x], tsum);
+            atomicAdd(&tv[e.y], tsum);
+          }
         }
       }
       __syncthreads();
@@ -666,19 +704,19 @@ constexpr bool kMedBatch[2] = {false, true};
 constexpr int kBigWin[2] = {14336, 28672};
 static_assert(kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
 
-template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH>
+template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH, bool VERT = false>
 static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, uint64_t nitems,
                        const unsigned long long* ostart, const uint32_t* owner_cnt,
                        const uint4* descs, const uint32_t* task_split, const uint32_t* task_idx,
-                       uint4* cursors, uint32_t* per_edge) {
+                       uint4* cursors, uint32_t* per_edge, unsigned long long* tv = nullptr) {
   if (nitems == 0) return TC_OK;
   cudaStream_t st = g->stream;
   const size_t smem = sizeof(uint4) * BUCKETS;
-  auto k = k_hash_intersect<M, THREADS, BUCKETS, WIN, MINB, BATCH>;
+  auto k = k_hash_intersect<M, THREADS, BUCKETS, WIN, MINB, BATCH, VERT>;
   TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t grid = std::min<uint64_t>(nitems, 0x7FFFFFFFull);
   launch(k, (unsigned)grid, THREADS, smem, st, g->off, g->cols, pcols, items, nitems, ostart,
-         owner_cnt, descs, task_split, task_idx, cursors, per_edge, g->ctrl.p);
+         owner_cnt, descs, task_split, task_idx, cursors, per_edge, g->cover.p, tv, g->ctrl.p);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -690,9 +728,11 @@ int merge_small_edges(tc_graph* g, int mode, const uint32_t* list,
                       const unsigned long long* nlist_dev, uint64_t nlist_max,
                       const int64_t* ustart, uint32_t* per_edge);
 
+// tv (cover mode, or NULL): per-vertex triangle counts are added to it
+// instead of the count alone.
 template <int M>
 static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const uint32_t* pcols,
-                           const int64_t* ustart, uint32_t* per_edge) {
+                           const int64_t* ustart, uint32_t* per_edge, unsigned long long* tv) {
   cudaStream_t st = g->stream;
   const int T = 256;
   DevBuf<uint32_t> owner_cnt, cursor, small_list, task_idx, task_split;
@@ -727,18 +767,33 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   TC_TRY(descs.alloc(ntasks, st));
   TC_TRY(cursors.alloc(ntasks, st));
   TC_TRY(task_split.alloc(ntasks, st));
-  if (per_edge) TC_TRY(task_idx.alloc(ntasks, st));
+  const bool need_idx = per_edge != nullptr || tv != nullptr;
+  if (need_idx) TC_TRY(task_idx.alloc(ntasks, st));
   TC_TRY(items0.alloc(nitems0, st));
   TC_TRY(items1.alloc(nitems1, st));
   if (ntasks > 0) {
     launch(k_bucket_scatter<M>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx, ostart.p,
            owner_work.p, cursor.p, descs.p, task_split.p,
-           per_edge ? task_idx.p : (uint32_t*)nullptr, small_list.p, g->ctrl.p);
+           need_idx ? task_idx.p : (uint32_t*)nullptr, small_list.p, g->ctrl.p);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
            kItemWork[M], items0.p, items1.p, counters.p);
   }
   TC_CUDA(cudaGetLastError());
   cudaEventRecord(g->ev[6], st);  // end of bucketing
+  if constexpr (M == kModeCover) {
+    if (tv) {
+      TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigWin[M], kBigPerSM, false, true>(
+          g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
+          cursors.p, nullptr, tv)));
+      TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedWin, kMedPerSM, false, true>(
+          g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
+          cursors.p, nullptr, tv)));
+      // the merge list's edges, with a sink per apex (find.cu)
+      if (nsmall > 0 || ntasks > 0)
+        TC_TRY(find_vertex_list(g, small_list.p, g->ctrl.p + kCtrlQ0, nidx, tv));
+      return TC_OK;
+    }
+  }
   TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigWin[M], kBigPerSM, false>(
       g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge)));
@@ -758,7 +813,7 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
 // nnz < 2^32 (32-bit task indices and row positions); callers fall back to
 // the merge kernels otherwise.
 int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge, int64_t first,
-               int64_t last) {
+               int64_t last, unsigned long long* tv) {
   EdgeSrc s{};
   s.off = g->off;
   s.cols = g->cols;
@@ -769,11 +824,11 @@ int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge,
     s.H = g->cover.p;
     s.hoff = g->hoff.p;
     s.seg = g->seg.p;
-    return hash_count_mode<kModeCover>(g, s, nidx, g->scols.p, ustart, per_edge);
+    return hash_count_mode<kModeCover>(g, s, nidx, g->scols.p, ustart, per_edge, tv);
   }
   s.erow = g->erow.p;
   s.ustart = ustart;
-  return hash_count_mode<kModePlain>(g, s, nidx, g->cols, ustart, per_edge);
+  return hash_count_mode<kModePlain>(g, s, nidx, g->cols, ustart, per_edge, nullptr);
 }
 
 }  // namespace tc

@@ -188,11 +188,21 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t fi
 int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry = nullptr, int64_t first = 0,
                 int64_t last = -1);
 
+// Hash intersection (hashsect.cu) over edges [first, last) of the mode's
+// index space; per_edge (per-edge counts) and tv (cover mode: per-vertex
+// counts) may be NULL.  Needs |edges| < 2^32 and nnz < 2^32.
+int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge, int64_t first,
+               int64_t last, unsigned long long* tv = nullptr);
+
 // Triangle finding (find.cu): per-vertex counts into tv_dev (n entries,
 // device), and the list of triangles (u, v, w) into out_dev (3 * cap
 // entries, device; *found = the number of triangles, which may exceed cap).
 int find_vertex_counts(tc_graph* g, unsigned long long* tv_dev);
 int find_list(tc_graph* g, uint32_t* out_dev, unsigned long long cap, uint64_t* found);
+// The same per-vertex counts for the cover edges whose H indices are
+// list[0 .. *nlist_dev) (device length, at most nlist_max).
+int find_vertex_list(tc_graph* g, const uint32_t* list, const unsigned long long* nlist_dev,
+                     uint64_t nlist_max, unsigned long long* tv_dev);
 
 // Work-balanced shard bounds of the mode's edge index space (shard.cu):
 // bounds_host[0] = 0 <= ... <= bounds_host[P] = |edges|.

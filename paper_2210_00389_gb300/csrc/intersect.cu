@@ -263,8 +263,7 @@ k_plain_intersect(const uint32_t* __restrict__ erow, int64_t nnz, const int64_t*
   block_add(elems, &ctrl[kCtrlElems]);
 }
 
-int hash_count(tc_graph* g, int mode, const int64_t* ustart, uint32_t* per_edge, int64_t first,
-               int64_t last);
+
 
 // Stage timings: ev4 -> ev6 bucketing, ev6 -> ev7 hash kernel, ev7 -> ev5
 // small-owner merge (the merge-only fallback records ev6 = ev7 = ev4).

@@ -46,7 +46,7 @@ constexpr uint32_t kSmallOwner = 64;              // owners this small use the m
 constexpr uint32_t kMediumMax = 2048;             // larger owners use the big tables
 // target lookups per work item, per mode (cover, plain): tuned on R-MAT
 // scale 20/22; larger items rebuild fewer tables, smaller ones balance better
-constexpr unsigned long long kItemWork[2] = {1ull << 21, 1ull << 19};
+constexpr unsigned long long kItemWork[2] = {1ull << 21, 1ull << 20};
 constexpr unsigned long long kBuildRatio = 4;     // hash an owner only if lookups >= 4 d(o)
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 

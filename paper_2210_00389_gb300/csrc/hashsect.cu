@@ -44,9 +44,22 @@ namespace tc {
 
 constexpr uint32_t kSmallOwner = 64;              // owners this small use the merge
 constexpr uint32_t kMediumMax = 2048;             // larger owners use the big tables
-// target lookups per work item, per mode (cover, plain): tuned on R-MAT
-// scale 20/22; larger items rebuild fewer tables, smaller ones balance better
-constexpr unsigned long long kItemWork[2] = {1ull << 21, 1ull << 20};
+// Lookups per work item, per mode (cover, plain): the step's total lookups
+// over (SMs x kItemsPerSM), clamped to [kItemMin, kItemMax].  Larger items
+// rebuild fewer tables, smaller ones balance better, and the best size grows
+// with the graph (measured on R-MAT scale 22 and 26 and Chung-Lu 2^23: cover
+// 2^21 .. 2^22 at scale 22, 2^23 at scale 26; plain 2^20 and 2^21).
+constexpr unsigned long long kItemMin[2] = {1ull << 21, 1ull << 20};
+constexpr unsigned long long kItemMax[2] = {1ull << 23, 1ull << 21};
+constexpr unsigned long long kItemsPerSM[2] = {64, 128};
+
+__device__ __forceinline__ unsigned long long item_work_of(const unsigned long long* ctrl,
+                                                           unsigned long long lo,
+                                                           unsigned long long hi,
+                                                           unsigned long long div) {
+  const unsigned long long w = ctrl[kCtrlWorkSum] / div;
+  return w < lo ? lo : (w > hi ? hi : w);
+}
 constexpr unsigned long long kBuildRatio = 4;     // hash an owner only if lookups >= 4 d(o)
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
@@ -130,6 +143,7 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
   const int lane = threadIdx.x & 31;
   uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long wsum = 0;  // this thread's share of the total lookups
   for (; base < nidx; base += stride) {
     const uint64_t idx = base + lane, gi = s.first + idx;
     bool small = false;
@@ -144,6 +158,7 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
         } else {
           key = o;
           work = desc_work(probe_desc<M>(s, gi, u, v, p)) + 1u;
+          wsum += work;
         }
       }
     }
@@ -167,6 +182,16 @@ __global__ void k_bucket_count(EdgeSrc s, uint64_t nidx, uint32_t* __restrict__ 
       b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
       if (small) small_list[b0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)gi;
     }
+  }
+  // the block's total lookups: one atomic per block
+  __shared__ unsigned long long red[32];
+  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_down_sync(0xFFFFFFFFu, wsum, o);
+  if (lane == 0) red[threadIdx.x >> 5] = wsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    if (t) atomicAdd(&ctrl[kCtrlWorkSum], t);
   }
 }
 
@@ -246,7 +271,9 @@ __device__ __forceinline__ int owner_class(uint32_t d) { return d > kMediumMax ?
 __global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
                               const uint32_t* __restrict__ owner_cnt,
                               const unsigned long long* __restrict__ owner_work,
-                              unsigned long long item_work, unsigned long long* ctrl) {
+                              unsigned long long item_lo, unsigned long long item_hi,
+                              unsigned long long item_div, unsigned long long* ctrl) {
+  const unsigned long long item_work = item_work_of(ctrl, item_lo, item_hi, item_div);
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long t[2] = {0ull, 0ull};
@@ -265,8 +292,11 @@ __global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
 __global__ void k_item_write(const int64_t* __restrict__ off, uint32_t n,
                              const uint32_t* __restrict__ owner_cnt,
                              const unsigned long long* __restrict__ owner_work,
-                             unsigned long long item_work, uint2* __restrict__ items0,
-                             uint2* __restrict__ items1, unsigned long long* cursors) {
+                             unsigned long long item_lo, unsigned long long item_hi,
+                             unsigned long long item_div, const unsigned long long* ctrl,
+                             uint2* __restrict__ items0, uint2* __restrict__ items1,
+                             unsigned long long* cursors) {
+  const unsigned long long item_work = item_work_of(ctrl, item_lo, item_hi, item_div);
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; o < (int64_t)n; o += stride) {
@@ -751,12 +781,14 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   TC_CUDA(cudaMemsetAsync(counters.p, 0, 4 * sizeof(unsigned long long), st));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlQ0, 0, sizeof(unsigned long long), st));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlItems, 0, 2 * sizeof(unsigned long long), st));
+  TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlWorkSum, 0, sizeof(unsigned long long), st));
+  const unsigned long long item_div = (unsigned long long)sm_count() * kItemsPerSM[M];
   launch(k_bucket_count<M>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx, owner_cnt.p,
          owner_work.p, small_list.p, g->ctrl.p);
   launch(k_u32_to_u64, grid_for(g->n, T), T, 0, st, owner_cnt.p, g->n, ostart.p);
   TC_TRY(exclusive_scan_u64(ostart.p, g->n, g->ctrl.p + kCtrlTmp, st));
   launch(k_item_counts, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-         kItemWork[M], g->ctrl.p);
+         kItemMin[M], kItemMax[M], item_div, g->ctrl.p);
   TC_CUDA(cudaGetLastError());
   TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
                           cudaMemcpyDeviceToHost, st));
@@ -776,7 +808,7 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
            owner_work.p, cursor.p, descs.p, task_split.p,
            need_idx ? task_idx.p : (uint32_t*)nullptr, small_list.p, g->ctrl.p);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-           kItemWork[M], items0.p, items1.p, counters.p);
+           kItemMin[M], kItemMax[M], item_div, g->ctrl.p, items0.p, items1.p, counters.p);
   }
   TC_CUDA(cudaGetLastError());
   cudaEventRecord(g->ev[6], st);  // end of bucketing

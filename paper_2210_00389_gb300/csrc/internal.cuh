@@ -162,6 +162,7 @@ enum CtrlSlot {
   kCtrlWork = 8,      // dynamic work counter of the intersection kernels
   kCtrlItems = 9,     // work items per table class (two slots: 9, 10)
   kCtrlLong = 11,     // chunks of long rows (ingest)
+  kCtrlWorkSum = 12,  // lookups of all hashed edges (bucketing)
   kCtrlSlots = 16
 };
 

@@ -448,3 +448,11 @@ def rmat_s26() -> CSR:
 
 def chung_lu_2_23() -> CSR:
     return chung_lu_islands(1 << 23, seed=7)
+
+
+def serve_large_specs() -> list[dict]:
+    """The serving stream's large requests: two R-MAT graphs per scale
+    18..22, edgefactor 16, edge seed 1000 + 10 scale + k, relabel stream
+    2000 + 10 scale + k (k = 0, 1)."""
+    return [dict(kind="rmat", scale=sc, edgefactor=16, seed=1000 + 10 * sc + k,
+                 relabel_seed=2000 + 10 * sc + k) for sc in range(18, 23) for k in range(2)]

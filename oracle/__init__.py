@@ -16,6 +16,9 @@ Functions (each cites the passage it follows in ``oracle.c``):
 * :func:`cetc_count`, :func:`cetc_edge_counts` — Alg. 1.
 * :func:`plain_count` — the direction-oriented edge iterator (Sec. I, V-A).
 * :func:`triangles` — triangle finding (lists {a < b < c}).
+* :func:`cetc_count_mt`, :func:`plain_count_mt`, :func:`cetc_all_edge_counts_mt`
+  — the same counting loops with the outer loop over vertices shared among
+  the host's cores (OpenMP), for the benchmark-size graphs.
 """
 from __future__ import annotations
 
@@ -36,8 +39,8 @@ def compile_source(src: str, out: str) -> str:
     """Compile an oracle C source file into a shared library at ``out``."""
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=os.path.dirname(out) or ".")
     os.close(fd)
-    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-fvisibility=hidden",
-                    src, "-o", tmp], check=True)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC",
+                    "-fvisibility=hidden", src, "-o", tmp], check=True)
     os.replace(tmp, out)
     return out
 
@@ -69,6 +72,13 @@ class Oracle:
                                             ctypes.c_int64, u32p]
         lib.or_plain_count.restype = ctypes.c_uint64
         lib.or_plain_count.argtypes = [ctypes.c_uint32, i64p, u32p]
+        lib.or_cetc_count_mt.restype = ctypes.c_uint64
+        lib.or_cetc_count_mt.argtypes = [ctypes.c_uint32, i64p, u32p, u32p, ctypes.c_int]
+        lib.or_plain_count_mt.restype = ctypes.c_uint64
+        lib.or_plain_count_mt.argtypes = [ctypes.c_uint32, i64p, u32p, ctypes.c_int]
+        lib.or_cetc_all_edge_counts_mt.restype = ctypes.c_int64
+        lib.or_cetc_all_edge_counts_mt.argtypes = [ctypes.c_uint32, i64p, u32p, u32p, u32p,
+                                                   ctypes.c_int64, ctypes.c_int]
         lib.or_triangles.restype = ctypes.c_int64
         lib.or_triangles.argtypes = [ctypes.c_uint32, i64p, u32p, u32p, ctypes.c_int64]
         self.lib = lib
@@ -100,6 +110,14 @@ class Oracle:
         assert h2 == h
         return uv[:h]
 
+    def num_cover(self, g, L) -> int:
+        """|H| without listing H (Thm. 1)."""
+        off, cols = _csr(g)
+        L = np.ascontiguousarray(L, dtype=np.uint32)
+        if L.size == 0:
+            return 0
+        return int(self.lib.or_cover_edges(g.n, _i64(off), _u32(cols), _u32(L), None, 0))
+
     def cetc_count(self, g, L) -> int:
         """T by Alg. 1 (exact uint64)."""
         off, cols = _csr(g)
@@ -126,6 +144,34 @@ class Oracle:
         """T by the direction-oriented edge iterator (u < v, w > v)."""
         off, cols = _csr(g)
         return int(self.lib.or_plain_count(g.n, _i64(off), _u32(cols)))
+
+    # all-core forms (OpenMP over the rows; threads = 0: all host cores)
+
+    def cetc_count_mt(self, g, L, threads: int = 0) -> int:
+        """T by Alg. 1, the outer loop shared among host threads."""
+        off, cols = _csr(g)
+        L = np.ascontiguousarray(L, dtype=np.uint32)
+        if L.size == 0:
+            return 0
+        return int(self.lib.or_cetc_count_mt(g.n, _i64(off), _u32(cols), _u32(L), threads))
+
+    def plain_count_mt(self, g, threads: int = 0) -> int:
+        """The plain edge iterator's T, the outer loop shared among threads."""
+        off, cols = _csr(g)
+        return int(self.lib.or_plain_count_mt(g.n, _i64(off), _u32(cols), threads))
+
+    def cetc_all_edge_counts_mt(self, g, L, num_cover: int, threads: int = 0) -> np.ndarray:
+        """Alg. 1's count of every cover edge, in H's ascending (u, v) order."""
+        off, cols = _csr(g)
+        L = np.ascontiguousarray(L, dtype=np.uint32)
+        out = np.zeros(max(num_cover, 1), dtype=np.uint32)
+        if g.n == 0:
+            return out[:0]
+        h = self.lib.or_cetc_all_edge_counts_mt(g.n, _i64(off), _u32(cols), _u32(L), _u32(out),
+                                                num_cover, threads)
+        if h != num_cover:
+            raise ValueError(f"|H| = {h}, expected {num_cover}")
+        return out[:h]
 
     def triangles(self, g) -> np.ndarray:
         """All triangles as an (T, 3) uint32 array of a < b < c."""
@@ -176,6 +222,10 @@ def cetc_count(g, L):
     return _default().cetc_count(g, L)
 
 
+def num_cover(g, L):
+    return _default().num_cover(g, L)
+
+
 def cetc_edge_counts(g, L, uv):
     return _default().cetc_edge_counts(g, L, uv)
 
@@ -186,6 +236,18 @@ def plain_count(g):
 
 def triangles(g):
     return _default().triangles(g)
+
+
+def cetc_count_mt(g, L, threads: int = 0):
+    return _default().cetc_count_mt(g, L, threads)
+
+
+def plain_count_mt(g, threads: int = 0):
+    return _default().plain_count_mt(g, threads)
+
+
+def cetc_all_edge_counts_mt(g, L, num_cover: int, threads: int = 0):
+    return _default().cetc_all_edge_counts_mt(g, L, num_cover, threads)
 
 
 def cetc(g, roots=None) -> dict:

@@ -34,6 +34,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <omp.h>
+
 #define OR_EXPORT __attribute__((visibility("default")))
 #define OR_UNVISITED 0xFFFFFFFFu
 
@@ -170,24 +172,103 @@ OR_EXPORT int or_cetc_edge_counts(uint32_t n, const int64_t* off, const uint32_t
 /* ------------------------------------------------------------------------ */
 /* The plain direction-oriented edge iterator (Sec. I and Sec. V-A): every
  * edge u < v, every common neighbour w > v, so each triangle a < b < c is
- * counted once, at its edge (a, b) with apex c. */
+ * counted once, at its edge (a, b) with apex c.  The common neighbours of
+ * one edge are found by the same two-pointer merge as above. */
+static uint64_t plain_edge_count(const int64_t* off, const uint32_t* cols, uint32_t u,
+                                 uint32_t v) {
+  uint64_t c = 0;
+  int64_t i = off[u], iend = off[u + 1];
+  int64_t j = off[v], jend = off[v + 1];
+  while (i < iend && j < jend) {
+    uint32_t a = cols[i], b = cols[j];
+    if (a < b) ++i;
+    else if (b < a) ++j;
+    else { if (a > v) ++c; ++i; ++j; }
+  }
+  return c;
+}
+
 OR_EXPORT uint64_t or_plain_count(uint32_t n, const int64_t* off, const uint32_t* cols) {
   uint64_t T = 0;
   for (uint32_t u = 0; u < n; ++u) {
     for (int64_t e = off[u]; e < off[u + 1]; ++e) {
       uint32_t v = cols[e];
-      if (!(u < v)) continue;
-      int64_t i = off[u], iend = off[u + 1];
-      int64_t j = off[v], jend = off[v + 1];
-      while (i < iend && j < jend) {
-        uint32_t a = cols[i], b = cols[j];
-        if (a < b) ++i;
-        else if (b < a) ++j;
-        else { if (a > v) ++T; ++i; ++j; }
-      }
+      if (u < v) T += plain_edge_count(off, cols, u, v);
     }
   }
   return T;
+}
+
+/* ------------------------------------------------------------------------ */
+/* All-core forms of the three counting loops above, for graphs too large
+ * for one core (R-MAT scale 22 and up).  Each is the single-threaded loop
+ * with its outer loop over u shared among `threads` OpenMP threads (0 = the
+ * OpenMP default) and the per-edge work unchanged: the same helpers, the
+ * same predicate, the same uint64 sums.  Rows are handed out in small
+ * dynamic chunks because hub rows cost far more than the rest. */
+OR_EXPORT uint64_t or_cetc_count_mt(uint32_t n, const int64_t* off, const uint32_t* cols,
+                                    const uint32_t* L, int threads) {
+  uint64_t T = 0;
+  if (threads <= 0) threads = omp_get_max_threads();
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 64) reduction(+ : T)
+  for (int64_t ui = 0; ui < (int64_t)n; ++ui) {
+    uint32_t u = (uint32_t)ui;
+    for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = cols[e];
+      if (L[u] == L[v] && u < v) T += cover_edge_count(off, cols, L, u, v);
+    }
+  }
+  return T;
+}
+
+OR_EXPORT uint64_t or_plain_count_mt(uint32_t n, const int64_t* off, const uint32_t* cols,
+                                     int threads) {
+  uint64_t T = 0;
+  if (threads <= 0) threads = omp_get_max_threads();
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 64) reduction(+ : T)
+  for (int64_t ui = 0; ui < (int64_t)n; ++ui) {
+    uint32_t u = (uint32_t)ui;
+    for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = cols[e];
+      if (u < v) T += plain_edge_count(off, cols, u, v);
+    }
+  }
+  return T;
+}
+
+/* Per-edge counts of Alg. 1 for every cover edge, in H's ascending (u, v)
+ * order: hstart[u] is the index in H of u's first cover edge (an exclusive
+ * prefix sum of the per-vertex cover-edge counts, computed here), so each
+ * thread writes the counts of its own rows.  At most cap counts are
+ * written; returns |H| (-1 if out of host memory). */
+OR_EXPORT int64_t or_cetc_all_edge_counts_mt(uint32_t n, const int64_t* off,
+                                             const uint32_t* cols, const uint32_t* L,
+                                             uint32_t* counts, int64_t cap, int threads) {
+  if (threads <= 0) threads = omp_get_max_threads();
+  int64_t* hstart = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+  if (!hstart) return -1;
+  hstart[0] = 0;
+  for (uint32_t u = 0; u < n; ++u) {
+    int64_t k = 0;
+    for (int64_t e = off[u]; e < off[u + 1]; ++e)
+      if (u < cols[e] && L[u] == L[cols[e]]) ++k;
+    hstart[u + 1] = hstart[u] + k;
+  }
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 64)
+  for (int64_t ui = 0; ui < (int64_t)n; ++ui) {
+    uint32_t u = (uint32_t)ui;
+    int64_t h = hstart[u];
+    for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = cols[e];
+      if (u < v && L[u] == L[v]) {
+        if (h < cap) counts[h] = (uint32_t)cover_edge_count(off, cols, L, u, v);
+        ++h;
+      }
+    }
+  }
+  int64_t total = hstart[n];
+  free(hstart);
+  return total;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -238,6 +238,11 @@ def check_brute_force(orc) -> list[str]:
             bad.append(f"{g.name}: cetc {r['T']} brute {len(tris)}")
         if orc.plain_count(g) != len(tris):
             bad.append(f"{g.name}: plain vs brute")
+        for th in (1, 3):
+            if orc.cetc_count_mt(g, r["levels"], th) != len(tris):
+                bad.append(f"{g.name}: all-core cetc ({th} threads) vs brute")
+            if orc.plain_count_mt(g, th) != len(tris):
+                bad.append(f"{g.name}: all-core plain ({th} threads) vs brute")
         lst = [tuple(map(int, t)) for t in orc.triangles(g)]
         if lst != tris:
             bad.append(f"{g.name}: enumerator list differs from brute force")
@@ -258,6 +263,9 @@ def check_brute_force(orc) -> list[str]:
             got = orc.cetc_edge_counts(g, L, r["H"]) if len(r["H"]) else np.zeros(0)
             if not np.array_equal(np.asarray(got, dtype=np.int64), want):
                 bad.append(f"{g.name}: per-edge counts differ from Thm. 2 accounting")
+            allc = orc.cetc_all_edge_counts_mt(g, L, len(want), 3)
+            if not np.array_equal(np.asarray(allc, dtype=np.int64), want):
+                bad.append(f"{g.name}: all-core per-edge counts differ from Thm. 2 accounting")
         except (AssertionError, KeyError) as e:
             bad.append(f"{g.name}: {e!r}")
     return bad
@@ -272,6 +280,8 @@ def check_trace(orc) -> list[str]:
             bad.append(f"{g.name}: cetc {r['T']} trace {t}")
         if orc.plain_count(g) != t:
             bad.append(f"{g.name}: plain vs trace")
+        if orc.cetc_count_mt(g, r["levels"], 4) != t or orc.plain_count_mt(g, 4) != t:
+            bad.append(f"{g.name}: all-core counts vs trace")
         roots = root_rule_roots(g)
         if not np.array_equal(r["levels"].astype(np.int64), scipy_levels(g, roots)):
             bad.append(f"{g.name}: levels vs scipy")
@@ -297,6 +307,8 @@ def check_root_invariance(orc, seed=5) -> list[str]:
                 bad.append(f"{g.name}: not a BFS labelling")
             if orc.cetc_count(g, L) != base:
                 bad.append(f"{g.name}: T depends on roots")
+            if orc.cetc_count_mt(g, L, 2) != base:
+                bad.append(f"{g.name}: all-core T depends on roots")
     return bad
 
 

@@ -220,9 +220,14 @@ def _sample_edges(H, k, seed):
     return np.sort(idx)
 
 
-def full_size_check(tc, g, nsample=20000):
+def full_size_check(tc, g):
+    """Levels, H, every per-edge count and T against the oracle in full (the
+    per-edge counts from the oracle's all-core loop), plus the plain path's
+    total."""
     ref_L, ref_nl = oracle.bfs_levels(g)
     ref_H = oracle.cover_edges(g, ref_L)
+    want = oracle.cetc_all_edge_counts_mt(g, ref_L, len(ref_H))
+    ref_T = int(want.sum(dtype=np.uint64))
     with tc.Graph(g.offsets, g.cols, flags=tc.TC_GRAPH_VALIDATE) as G:
         L, nl = G.levels()
         assert nl == ref_nl
@@ -231,22 +236,17 @@ def full_size_check(tc, g, nsample=20000):
         assert np.array_equal(H, ref_H)
         T = G.count(tc.TC_MODE_COVER)
         c = G.cover_edge_counts()
-        assert int(c.astype(np.uint64).sum()) == T
-        # sampled per-edge counts (uniform + the heaviest-degree edges)
-        deg = g.degrees()
-        heavy = np.argsort(-(deg[ref_H[:, 0]] + deg[ref_H[:, 1]]), kind="stable")[:500]
-        idx = np.unique(np.concatenate([_sample_edges(ref_H, nsample, 3), heavy]))
-        want = oracle.cetc_edge_counts(g, ref_L, ref_H[idx])
-        assert np.array_equal(c[idx], want)
-        # the plain all-edge path finds the same total
-        assert G.count(tc.TC_MODE_PLAIN) == T
-    return T
+        bad = np.nonzero(c != want)[0]
+        assert bad.size == 0, f"{bad.size} edges differ, first {ref_H[bad[:5]].tolist()}"
+        assert T == ref_T
+        assert G.count(tc.TC_MODE_PLAIN) == ref_T
+    return ref_T
 
 
 @pytest.mark.slow
 def test_full_rmat_s22(tc):
-    """R-MAT scale 22, edgefactor 16, relabelled: levels and H in full,
-    per-edge counts sampled, cover T == plain T == sum of per-edge counts."""
+    """R-MAT scale 22, edgefactor 16, relabelled: levels, H, all 34M per-edge
+    counts and T against the oracle; the plain path's T too."""
     g = gg.rmat_s22()
     T = full_size_check(tc, g)
     # sanity range only: the paper's fit 77.422 n^1.125 is ~2.2e9 at this size
@@ -258,3 +258,35 @@ def test_full_chung_lu(tc):
     """Chung-Lu n = 2^23 with degree cap 65,536 and Erdos-Renyi islands."""
     g = gg.chung_lu_2_23()
     full_size_check(tc, g)
+
+
+@pytest.mark.slow
+def test_full_rmat_s26(tc):
+    """R-MAT scale 26 (the serving workload's resident graph: n = 2^26,
+    nnz ~2.1e9, CSR offsets near the top of the 32-bit range the kernels'
+    descriptors hold): levels and H against the oracle in full; per-edge
+    counts on a sample of 20,000 uniform edges, the 500 heaviest and the
+    500 whose rows sit highest in the CSR; cover T == plain T == the sum
+    of the per-edge counts."""
+    g = gg.rmat_s26()
+    assert g.nnz > 2_000_000_000
+    ref_L, ref_nl = oracle.bfs_levels(g)
+    ref_H = oracle.cover_edges(g, ref_L)
+    deg = g.degrees()
+    heavy = np.argsort(-(deg[ref_H[:, 0]].astype(np.int64) + deg[ref_H[:, 1]]),
+                       kind="stable")[:500]
+    idx = np.unique(np.concatenate([_sample_edges(ref_H, 20000, 3), heavy,
+                                    np.arange(len(ref_H) - 500, len(ref_H))]))
+    want = oracle.cetc_edge_counts(g, ref_L, ref_H[idx])
+    with tc.Graph(g.offsets, g.cols) as G:
+        L, nl = G.levels()
+        assert nl == ref_nl
+        assert np.array_equal(L, ref_L)
+        H = G.cover_edges()
+        assert np.array_equal(H, ref_H)
+        del H
+        T = G.count(tc.TC_MODE_COVER)
+        c = G.cover_edge_counts()
+        assert np.array_equal(c[idx], want)
+        assert int(c.sum(dtype=np.uint64)) == T
+        assert G.count(tc.TC_MODE_PLAIN) == T

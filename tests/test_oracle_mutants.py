@@ -20,7 +20,8 @@ MUTANTS = [
      "if (L[u] != L[w] || (L[u] == L[w] && v < w)) ++c;",
      "if (L[u] != L[w] || (L[u] == L[w] && w < v)) ++c;"),
     ("count visits both directions of a cover edge",
-     "if (L[u] == L[v] && u < v) T += cover_edge_count", "if (L[u] == L[v]) T += cover_edge_count"),
+     "if (L[u] == L[v] && u < v) T += cover_edge_count(off, cols, L, u, v);\n    }\n  }\n  return T;\n}\n\n/* Per-edge counts",
+     "if (L[u] == L[v]) T += cover_edge_count(off, cols, L, u, v);\n    }\n  }\n  return T;\n}\n\n/* Per-edge counts"),
     ("level not incremented", "L[y] = L[x] + 1;", "L[y] = L[x];"),
     ("root tie-break picks the highest id",
      "if (off[v + 1] - off[v] > off[r0 + 1] - off[r0]) r0 = v;",
@@ -30,11 +31,20 @@ MUTANTS = [
     ("unvisited components never restarted",
      "if (L[v] == OR_UNVISITED) bfs_from(v, off, cols, L, queue);", ";"),
     ("cover set keeps both orientations",
-     "if (u < v && L[u] == L[v]) {", "if (u != v && L[u] == L[v]) {"),
+     "if (u < v && L[u] == L[v]) {\n        if (uv && h < cap)",
+     "if (u != v && L[u] == L[v]) {\n        if (uv && h < cap)"),
     ("cover set keeps level-crossing edges",
-     "if (u < v && L[u] == L[v]) {", "if (u < v) {"),
-    ("plain apex cut against u", "else { if (a > v) ++T; ++i; ++j; }",
-     "else { if (a > u) ++T; ++i; ++j; }"),
+     "if (u < v && L[u] == L[v]) {\n        if (uv && h < cap)", "if (u < v) {\n        if (uv && h < cap)"),
+    ("plain apex cut against u", "else { if (a > v) ++c; ++i; ++j; }",
+     "else { if (a > u) ++c; ++i; ++j; }"),
+    ("all-core cover loop keeps both orientations",
+     "if (L[u] == L[v] && u < v) T += cover_edge_count(off, cols, L, u, v);\n    }\n  }\n  return T;\n}\n\nOR_EXPORT uint64_t or_plain_count_mt",
+     "if (L[u] == L[v]) T += cover_edge_count(off, cols, L, u, v);\n    }\n  }\n  return T;\n}\n\nOR_EXPORT uint64_t or_plain_count_mt"),
+    ("all-core plain loop takes u > v too",
+     "      if (u < v) T += plain_edge_count(off, cols, u, v);\n    }\n  }\n  return T;\n}\n\n/* Per-edge",
+     "      if (u != v) T += plain_edge_count(off, cols, u, v);\n    }\n  }\n  return T;\n}\n\n/* Per-edge"),
+    ("all-edge counts skip the level test",
+     "if (u < v && L[u] == L[v]) {\n        if (h < cap)", "if (u < v) {\n        if (h < cap)"),
     ("enumerator apex cut dropped", "if (x > b) {", "if (x != b) {"),
     ("merge advances the wrong list", "if (a < b) {\n      ++i;", "if (a < b) {\n      ++j;"),
 ]

@@ -11,9 +11,11 @@ other parity test.  This file is collected last on purpose.
 """
 import ctypes
 
+import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +42,41 @@ def test_static_plain_count_matches_tc_count():
             assert st == tc.TC_OK, tc.tc_last_error()
             torch.cuda.synchronize()
             assert int(out.item()) == want
+
+
+def _spread(g, n, seed):
+    """g's edges with its vertices placed at random distinct ids of [0, n),
+    the last id included, so a graph of n vertices with few edges."""
+    rng = np.random.default_rng(seed)
+    ids = np.sort(rng.choice(n - 1, size=g.n - 1, replace=False)).astype(np.uint32)
+    ids = np.append(ids, np.uint32(n - 1))
+    rng.shuffle(ids)
+    u, v = gg.to_edge_list(g)
+    return gg.from_edges(n, ids[u], ids[v], name=f"{g.name}-in-{n}")
+
+
+def test_static_plain_count_at_capacity_vs_oracle():
+    """n = 4,194,304, the scratch's exact capacity (every upper-start slot of
+    the static array in use), and a small graph: the count against the
+    CPU oracle's plain edge iterator and Alg. 1 count, two calls in a row."""
+    import torch
+    import paper_2210_00389_gb300 as tc
+
+    stream = torch.cuda.current_stream()
+    for g in (_spread(gg.rmat(14, 16, seed=21), 1 << 22, 5), gg.rmat(9, 8, seed=3)):
+        want = oracle.plain_count(g)
+        assert want == oracle.cetc(g)["T"]
+        off = torch.from_numpy(g.offsets).cuda()
+        cols = torch.from_numpy(g.cols).cuda()
+        out = torch.empty(1, dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            out.fill_(-1)
+            st = tc._lib.tc_count_plain_static(off.data_ptr(), cols.data_ptr(), g.n, g.nnz,
+                                               out.data_ptr(),
+                                               ctypes.c_void_p(stream.cuda_stream))
+            assert st == tc.TC_OK, tc.tc_last_error()
+            torch.cuda.synchronize()
+            assert int(out.item()) == want, g.name
 
 
 def test_static_plain_count_rejects_oversized_graphs():

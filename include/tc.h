@@ -21,8 +21,11 @@
  *    the GPU, anything else is treated as host memory.
  *  - Every call on a tc_graph runs on the CUDA stream given at creation and
  *    returns only after its results are complete and visible to the host.
- *  - A tc_graph may be used by one thread at a time; different graphs and
- *    servers are independent.
+ *  - Thread safety: calls on one tc_graph from several host threads are
+ *    serialized by a lock inside the graph (each call runs alone on the
+ *    graph's stream); tc_graph_destroy must not overlap any other call on
+ *    the same graph.  Different graphs are independent; a tc_server takes
+ *    calls from any thread.
  *  - Device faults are never raised on purpose: device-side checks set an
  *    error word that the host turns into a status code.
  */
@@ -153,10 +156,17 @@ enum {
                         u < v, counting common neighbours w > v (Sec. I, V-A) */
 };
 
+/* Intersection technique (Sec. V-A lists merging, binary search and
+ * hashing): OR'ed into tc_count's mode, TC_INTERSECT_MERGE counts with the
+ * warp-per-edge merge / binary-search kernels instead of the owner-grouped
+ * hash intersection (same result; a comparison arm). */
+enum { TC_INTERSECT_MERGE = 0x10 };
+
 /* Exact triangle count T (uint64, host pointer count_out).  TC_MODE_COVER
  * runs BFS + cover extraction if not cached, then the intersection with the
  * count-once rule and the reduction; TC_MODE_PLAIN runs the intersection
- * over every edge.  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA. */
+ * over every edge.  mode may carry TC_INTERSECT_MERGE.
+ * Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA. */
 TC_API int tc_count(tc_graph* g, int mode, uint64_t* count_out);
 
 /* Per-cover-edge counts of Alg. 1: counts_out[i] = number of w that
@@ -233,7 +243,10 @@ TC_API int tc_graph_stats(const tc_graph* g, tc_stats_t* out);
  * most 4,194,304 (TC_ERR_CAPACITY beyond it, checked before any work).  The
  * first call on a device looks up that device's scratch address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
+ * stream capture.  The cached address belongs to the CUDA context current
+ * at that first call: after cudaDeviceReset (or anything else that destroys
+ * the device's primary context) the cache is stale, so do not call this
+ * entry point again in that process.  All calls share the array: calls that overlap on the GPU
  * race and give wrong counts, so serialize them (one stream, or events).
  * Errors: TC_ERR_CAPACITY, TC_ERR_INVALID_ARG (NULL, nnz < 0, or a pointer
  * that is not device memory), TC_ERR_CUDA. */

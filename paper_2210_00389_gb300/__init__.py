@@ -47,6 +47,7 @@ TC_GRAPH_BORROW = 4
 
 TC_MODE_COVER = 0
 TC_MODE_PLAIN = 1
+TC_INTERSECT_MERGE = 0x10
 
 
 class CSRView(ctypes.Structure):

@@ -36,6 +36,7 @@ int tc_bfs_levels(tc_graph* g, const uint32_t* roots, uint32_t nroots, uint32_t*
                   uint32_t* nlevels_out) {
   if (!g) return fail(TC_ERR_INVALID_ARG, "tc_bfs_levels: NULL graph");
   if (roots && nroots == 0) roots = nullptr;
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   cudaEventRecord(g->ev[0], g->stream);
   TC_TRY(compute_levels(g, roots, nroots));
@@ -52,6 +53,7 @@ int tc_bfs_levels(tc_graph* g, const uint32_t* roots, uint32_t nroots, uint32_t*
 int tc_cover_edges(tc_graph* g, uint32_t* uv_out, int64_t cap, int64_t* count_out) {
   if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_cover_edges: NULL argument");
   if (uv_out && cap < 0) return fail(TC_ERR_INVALID_ARG, "tc_cover_edges: cap < 0");
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   cudaEventRecord(g->ev[0], g->stream);
   if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
@@ -75,8 +77,11 @@ int tc_cover_edges(tc_graph* g, uint32_t* uv_out, int64_t cap, int64_t* count_ou
 
 int tc_count(tc_graph* g, int mode, uint64_t* count_out) {
   if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_count: NULL argument");
+  const bool merge_only = (mode & TC_INTERSECT_MERGE) != 0;
+  mode &= ~TC_INTERSECT_MERGE;
   if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
     return fail(TC_ERR_INVALID_ARG, "tc_count: unknown mode %d", mode);
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   tc_stats_t& st = g->stats;
   st.ms_bfs = st.ms_cover = st.ms_bucket = st.ms_intersect = st.ms_total = 0.f;
@@ -88,7 +93,7 @@ int tc_count(tc_graph* g, int mode, uint64_t* count_out) {
     cudaEventRecord(g->ev[1], g->stream);
     if (g->num_cover < 0) TC_TRY(compute_cover(g));
     cudaEventRecord(g->ev[2], g->stream);
-    TC_TRY(count_cover(g, nullptr, &T));
+    TC_TRY(count_cover(g, nullptr, &T, 0, -1, merge_only));
     cudaEventRecord(g->ev[3], g->stream);
     cudaEventSynchronize(g->ev[3]);
     st.ms_bfs = elapsed(g->ev[0], g->ev[1]);
@@ -96,7 +101,7 @@ int tc_count(tc_graph* g, int mode, uint64_t* count_out) {
     st.ms_total = elapsed(g->ev[0], g->ev[3]);
   } else {
     cudaEventRecord(g->ev[1], g->stream);
-    TC_TRY(count_plain(g, &T));
+    TC_TRY(count_plain(g, &T, nullptr, 0, -1, merge_only));
     cudaEventRecord(g->ev[3], g->stream);
     cudaEventSynchronize(g->ev[3]);
     st.ms_total = elapsed(g->ev[0], g->ev[3]);
@@ -109,6 +114,7 @@ int tc_count(tc_graph* g, int mode, uint64_t* count_out) {
 int tc_vertex_counts(tc_graph* g, uint64_t* counts_out) {
   if (!g || (!counts_out && g->n > 0))
     return fail(TC_ERR_INVALID_ARG, "tc_vertex_counts: NULL argument");
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   if (g->n == 0) return TC_OK;
   if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
@@ -124,6 +130,7 @@ int tc_vertex_counts(tc_graph* g, uint64_t* counts_out) {
 int tc_list_triangles(tc_graph* g, uint32_t* tri_out, int64_t cap, int64_t* count_out) {
   if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_list_triangles: NULL argument");
   if (tri_out && cap < 0) return fail(TC_ERR_INVALID_ARG, "tc_list_triangles: cap < 0");
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
   if (g->num_cover < 0) TC_TRY(compute_cover(g));
@@ -159,6 +166,7 @@ int tc_shard_bounds(tc_graph* g, int mode, int32_t nshards, int64_t* bounds_out)
   if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
     return fail(TC_ERR_INVALID_ARG, "tc_shard_bounds: unknown mode %d", mode);
   if (nshards < 1) return fail(TC_ERR_INVALID_ARG, "tc_shard_bounds: nshards < 1");
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   if (mode == TC_MODE_COVER && g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
   return shard_bounds(g, mode, nshards, bounds_out);
@@ -168,6 +176,7 @@ int tc_count_range(tc_graph* g, int mode, int64_t begin, int64_t end, uint64_t* 
   if (!g || !count_out) return fail(TC_ERR_INVALID_ARG, "tc_count_range: NULL argument");
   if (mode != TC_MODE_COVER && mode != TC_MODE_PLAIN)
     return fail(TC_ERR_INVALID_ARG, "tc_count_range: unknown mode %d", mode);
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   if (mode == TC_MODE_COVER) {
     if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
@@ -188,6 +197,7 @@ int tc_count_range(tc_graph* g, int mode, int64_t begin, int64_t end, uint64_t* 
 
 int tc_cover_edge_counts(tc_graph* g, uint32_t* counts_out, int64_t cap) {
   if (!g || !counts_out) return fail(TC_ERR_INVALID_ARG, "tc_cover_edge_counts: NULL argument");
+  std::lock_guard<std::mutex> lk(g->mu);
   DeviceGuard dg(g->device);
   if (g->num_cover < 0) TC_TRY(compute_cover(g));
   if (g->num_cover > cap)

@@ -385,6 +385,20 @@ static int make_descs(const tc_csr_view* graphs, const std::vector<int32_t>& idx
   return TC_OK;
 }
 
+// One cached executable graph per host thread and device (see run_tiny).
+struct ExecCache {
+  cudaGraphExec_t exec = nullptr;
+  ~ExecCache() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+static ExecCache& exec_cache() {
+  thread_local ExecCache per_device[16];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return per_device[dev >= 0 && dev < 16 ? dev : 0];
+}
+
 // Tiny members: one persistent launch, captured into a CUDA graph on `cs`
 // and replayed on `user`.
 static int run_tiny(const tc_csr_view* graphs, const std::vector<int32_t>& idx, int mode,
@@ -430,7 +444,22 @@ static int run_tiny(const tc_csr_view* graphs, const std::vector<int32_t>& idx, 
     launch_batch<512>(grid, cs, dgraphs.p, dorder.p, ng, mode, skew, scratch.p, max_n, dcounts.p,
                       dstatus.p, dqueue.p);
   TC_CUDA(cudaStreamEndCapture(cs, &cg));
-  cudaError_t e = cudaGraphInstantiate(&exec, cg, 0);
+  // The executable graph is kept per host thread and device: a later call
+  // captures its own (same-shaped) graph and updates the cached executable
+  // in place with the new parameters instead of instantiating it again; a
+  // capture of another shape (another block size) re-instantiates.
+  ExecCache& ec = exec_cache();
+  cudaError_t e = cudaSuccess;
+  if (ec.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ec.exec, cg, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(ec.exec);
+      ec.exec = nullptr;
+    }
+  }
+  if (!ec.exec) e = cudaGraphInstantiate(&ec.exec, cg, 0);
+  exec = ec.exec;
   if (e == cudaSuccess) e = cudaGraphLaunch(exec, user);
   std::vector<unsigned long long> c(hg.size());
   std::vector<int> s(hg.size());
@@ -440,7 +469,6 @@ static int run_tiny(const tc_csr_view* graphs, const std::vector<int32_t>& idx, 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s.data(), dstatus.p, sizeof(int) * s.size(), cudaMemcpyDeviceToHost, user);
   if (e == cudaSuccess) e = cudaStreamSynchronize(user);
-  if (exec) cudaGraphExecDestroy(exec);
   if (cg) cudaGraphDestroy(cg);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch", __FILE__, __LINE__);
   for (size_t k = 0; k < idx.size(); ++k) {

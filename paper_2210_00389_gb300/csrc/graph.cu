@@ -340,12 +340,14 @@ int tc_graph_destroy(tc_graph* g) {
 
 int tc_graph_invalidate(tc_graph* g) {
   if (!g) return fail(TC_ERR_INVALID_ARG, "tc_graph_invalidate: NULL graph");
+  std::lock_guard<std::mutex> lk(g->mu);
   graph_drop_cache(g);
   return TC_OK;
 }
 
 int tc_graph_info(const tc_graph* g, tc_graph_info_t* info) {
   if (!g || !info) return fail(TC_ERR_INVALID_ARG, "tc_graph_info: NULL argument");
+  std::lock_guard<std::mutex> lk(g->mu);
   info->n = g->n;
   info->nnz = g->nnz;
   info->num_edges = g->nnz / 2;
@@ -358,6 +360,7 @@ int tc_graph_info(const tc_graph* g, tc_graph_info_t* info) {
 
 int tc_graph_stats(const tc_graph* g, tc_stats_t* out) {
   if (!g || !out) return fail(TC_ERR_INVALID_ARG, "tc_graph_stats: NULL argument");
+  std::lock_guard<std::mutex> lk(g->mu);
   *out = g->stats;
   return TC_OK;
 }

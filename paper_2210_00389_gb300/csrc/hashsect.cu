@@ -482,11 +482,35 @@ __device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0
                                                  const uint32_t* Q2, uint32_t m2,
                                                  const BucketT* tab, uint32_t nb,
                                                  Sink sink = Sink()) {
-  const uint32_t f0 = m0 - m0 % kGroup, f1 = m1 - m1 % kGroup, f2 = m2 - m2 % kGroup;
+  const uint32_t g0 = m0 / kGroup, g1 = m1 / kGroup, g2 = m2 / kGroup;
+  const uint32_t g01 = g0 + g1, ng = g01 + g2;
   unsigned c = 0;
-  for (uint32_t k = 0; k < f0; k += kGroup) c += probe_group_full(Q0 + k, tab, nb, sink);
-  for (uint32_t k = 0; k < f1; k += kGroup) c += probe_group_full(Q1 + k, tab, nb, sink);
-  for (uint32_t k = 0; k < f2; k += kGroup) c += probe_group_full(Q2 + k, tab, nb, sink);
+  if (ng > 0) {
+    const int lane = threadIdx.x & 31;
+    auto group_ptr = [&](uint32_t g) {
+      return g < g0 ? Q0 + g * kGroup
+                    : (g < g01 ? Q1 + (g - g0) * kGroup : Q2 + (g - g01) * kGroup);
+    };
+    bool ok[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) ok[j] = true;
+    uint32_t cur[kUnroll], nxt[kUnroll];
+    {
+      const uint32_t* gp = group_ptr(0);
+#pragma unroll
+      for (int j = 0; j < kUnroll; ++j) cur[j] = __ldg(gp + j * 32 + lane);
+    }
+    for (uint32_t g = 1; g < ng; ++g) {
+      const uint32_t* gp = group_ptr(g);
+#pragma unroll
+      for (int j = 0; j < kUnroll; ++j) nxt[j] = __ldg(gp + j * 32 + lane);
+      c += table_find_n<kUnroll>(tab, nb, cur, ok, sink);
+#pragma unroll
+      for (int j = 0; j < kUnroll; ++j) cur[j] = nxt[j];
+    }
+    c += table_find_n<kUnroll>(tab, nb, cur, ok, sink);
+  }
+  const uint32_t f0 = g0 * kGroup, f1 = g1 * kGroup, f2 = g2 * kGroup;
   const uint32_t r0 = m0 - f0, s1 = r0 + (m1 - f1), tt = s1 + (m2 - f2);
   const uint32_t* R0 = Q0 + f0;
   const uint32_t* R1 = Q1 + f1 - r0;

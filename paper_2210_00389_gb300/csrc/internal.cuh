@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <cstddef>
+#include <mutex>
 #include <utility>
 
 #include "tc.h"
@@ -106,6 +107,9 @@ int sm_count();
 
 // The opaque graph object.
 struct tc_graph {
+  // held by every entry point that takes the graph (except destroy), so
+  // calls on one graph from several host threads run one after another
+  mutable std::mutex mu;
   int device = 0;
   cudaStream_t stream = nullptr;
   uint32_t n = 0;
@@ -184,10 +188,12 @@ int compute_cover(tc_graph* g);
 // H in its canonical order; plain: CSR entries, those with u > v adding
 // nothing); last < 0 means to the end.  Per-edge outputs are indexed by the
 // global edge index.
+// merge_only: the warp merge / binary-search kernels of intersect.cu
+// instead of the hash intersection (a comparison arm).
 int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t first = 0,
-                int64_t last = -1);
+                int64_t last = -1, bool merge_only = false);
 int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry = nullptr, int64_t first = 0,
-                int64_t last = -1);
+                int64_t last = -1, bool merge_only = false);
 
 // Hash intersection (hashsect.cu) over edges [first, last) of the mode's
 // index space; per_edge (per-edge counts) and tv (cover mode: per-vertex

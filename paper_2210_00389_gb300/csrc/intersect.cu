@@ -291,7 +291,7 @@ static int set_work_start(tc_graph* g, int64_t first) {
 }
 
 int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t first,
-                int64_t last) {
+                int64_t last, bool merge_only) {
   cudaStream_t s = g->stream;
   if (g->num_cover < 0) TC_TRY(compute_cover(g));
   if (last < 0 || last > g->num_cover) last = g->num_cover;
@@ -302,7 +302,8 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t fi
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
   if (per_edge_out && g->num_cover > 0)
     TC_CUDA(cudaMemsetAsync(per_edge_out, 0, sizeof(uint32_t) * (size_t)g->num_cover, s));
-  const bool hashed = g->num_cover < (int64_t)0xFFFFFFFFll && g->nnz < (int64_t)0xFFFFFFFFll;
+  const bool hashed = !merge_only && g->num_cover < (int64_t)0xFFFFFFFFll &&
+                      g->nnz < (int64_t)0xFFFFFFFFll;
   cudaEventRecord(g->ev[4], s);
   if (hashed) {
     TC_TRY(hash_count(g, 0, nullptr, per_edge_out, first, last));
@@ -324,7 +325,8 @@ int count_cover(tc_graph* g, uint32_t* per_edge_out, uint64_t* total, int64_t fi
 
 // per_entry (device, nnz entries, or NULL): the count of every CSR entry
 // (u, v) with u < v; other entries are left 0.  Entries [first, last).
-int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry, int64_t first, int64_t last) {
+int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry, int64_t first, int64_t last,
+                bool merge_only) {
   cudaStream_t s = g->stream;
   if (last < 0 || last > g->nnz) last = g->nnz;
   if (first < 0) first = 0;
@@ -333,7 +335,7 @@ int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry, int64_t first
   TC_TRY(set_work_start(g, first));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlElems, 0, sizeof(unsigned long long), s));
   g->stats.ms_intersect = g->stats.ms_bucket = g->stats.ms_main_kernel = 0.f;
-  const bool hashed = g->nnz < (int64_t)0xFFFFFFFFll;
+  const bool hashed = !merge_only && g->nnz < (int64_t)0xFFFFFFFFll;
   if (per_entry && !hashed)
     return fail(TC_ERR_CAPACITY, "per-entry plain counts need nnz < 2^32");
   DevBuf<int64_t> ustart;

@@ -290,3 +290,26 @@ def test_full_rmat_s26(tc):
         assert np.array_equal(c[idx], want)
         assert int(c.sum(dtype=np.uint64)) == T
         assert G.count(tc.TC_MODE_PLAIN) == T
+    # the oracle's full count of this graph, when the stored file has it
+    # (tests/golden/make_golden_large.py: all-core Alg. 1 and plain loops)
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "large_counts.json")
+    gold = json.load(open(path)).get("rmat_s26") if os.path.exists(path) else None
+    if gold is not None:
+        assert gold["nnz"] == g.nnz and gold["num_cover"] == len(ref_H)
+        assert gold["nlevels"] == ref_nl
+        assert T == gold["T"]
+
+
+def test_merge_technique_arm(tc):
+    """TC_INTERSECT_MERGE (warp merge / binary search instead of hashing,
+    Sec. V-A) gives the oracle's T in both modes, on a multi-tile R-MAT with
+    hub rows, a Chung-Lu graph with islands and a closed form."""
+    for g in (gg.rmat(15, 16, seed=4, relabel_seed=5),
+              gg.chung_lu_islands(1 << 14, mean_degree=12, cap=1024, seed=3), gg.wheel(70)):
+        T = oracle.cetc(g)["T"]
+        with tc.Graph(g.offsets, g.cols) as G:
+            for mode in (tc.TC_MODE_COVER, tc.TC_MODE_PLAIN):
+                assert G.count(mode | tc.TC_INTERSECT_MERGE) == T, (g.name, mode)
+                assert G.count(mode) == T

@@ -83,3 +83,23 @@ def test_count_sharded_single_process(tc):
             P = 4
             locals_ = [count_sharded(G, mode, r, P, lambda x: x)[0] for r in range(P)]
             assert sum(locals_) == T
+
+
+@pytest.mark.parametrize("mode_name", ["cover", "plain"])
+def test_shard_balance_rmat18(tc, mode_name):
+    """Slices of tc_shard_bounds balance the intersection's real work: on
+    R-MAT scale 18 (relabelled) with 8 virtual shards, the list elements each
+    slice's count handles (counted by the kernels) stay within 1.35x of the
+    mean, and the slices add up to the oracle's T."""
+    g = gg.rmat(18, 16, seed=2, relabel_seed=2 + 2**32)
+    T = oracle.cetc_count_mt(g, oracle.bfs_levels(g)[0])
+    mode = tc.TC_MODE_COVER if mode_name == "cover" else tc.TC_MODE_PLAIN
+    P = 8
+    with tc.Graph(g.offsets, g.cols, n=g.n) as G:
+        b = G.shard_bounds(mode, P)
+        parts, elems = [], []
+        for k in range(P):
+            parts.append(G.count_range(mode, int(b[k]), int(b[k + 1])))
+            elems.append(G.stats()["list_elems"])
+    assert sum(parts) == T
+    assert max(elems) <= 1.35 * (sum(elems) / P), elems

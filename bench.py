@@ -19,8 +19,16 @@ Also measured in the same run:
   * the CPU oracle on a bounded sample of the same workload (rank 0, N=1).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun every rank counts its own graph of the same recipe (seeded by
-rank): independent problems, weak scaling, no collective on the data path.
+Under torchrun the ranks count ONE graph together by default (--shard):
+each rank counts a work-balanced slice of the cover edges and the slice
+counts are summed by one int64 all-reduce (strong scaling); with
+--no-shard every rank counts its own graph of the same recipe (weak
+scaling, no collective on the data path).
+
+The default single-GPU line also carries the batched (4,096 mixed graphs)
+and serving (resident R-MAT scale 26 + a Poisson request stream)
+configurations of the same metric, and the CPU oracle measured in full on
+all host cores.
 """
 from __future__ import annotations
 
@@ -52,7 +60,7 @@ def parse_args():
     ap.add_argument("--workload", default="rmat22",
                     choices=["rmat22", "rmat10", "rmat18", "rmat20", "rmat26", "chunglu23",
                              "batch", "serve", "kstudy"])
-    ap.add_argument("--kstudy-max-scale", type=int, default=24,
+    ap.add_argument("--kstudy-max-scale", type=int, default=26,
                     help="kstudy: largest R-MAT scale (from 6)")
     ap.add_argument("--requests", type=int, default=20000, help="serve: stream length")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
@@ -60,9 +68,26 @@ def parse_args():
     ap.add_argument("--arm", default="all", choices=["all", "cover", "plain"],
                     help="'cover' or 'plain' runs only that device-resident arm "
                          "(for profiling one step); 'all' is the benchmark")
+    ap.add_argument("--intersect", default="hash", choices=["hash", "merge"],
+                    help="with --arm: the owner-grouped hash intersection (the product "
+                         "path) or the warp merge / binary-search kernels (Sec. V-A's other "
+                         "two techniques), same graph, same result")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-runs", type=int, default=1,
+                    help="runs of the all-core oracle in the default line (median)")
+    ap.add_argument("--ref-sample-div", type=int, default=16,
+                    help="reference arm: each step counts 1/this of the cover edges")
+    ap.add_argument("--shard", dest="shard", action="store_true", default=None,
+                    help="count one graph with all ranks (edge-range shards, strong "
+                         "scaling); the default under torchrun")
+    ap.add_argument("--no-shard", dest="shard", action="store_false",
+                    help="under torchrun: every rank counts its own graph (weak scaling)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default workload: skip the batch object")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="default workload: skip the serve object")
     return ap.parse_args()
 
 
@@ -218,15 +243,53 @@ def oracle_sample(g, target_s: float, seed: int = 0):
 
 
 def cpu_info():
+    """Host core count and CPU model name (lscpu's "Model name", which names
+    Arm cores too, else /proc/cpuinfo's)."""
     model = ""
     try:
-        for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part", "hardware")):
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
                 model = line.split(":", 1)[1].strip()
                 break
     except Exception:
         pass
-    return {"host_cores": os.cpu_count(), "cpu": model}
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu": model or "unknown"}
+
+
+def oracle_full_all_cores(g, runs: int = 1):
+    """The CPU oracle's Alg. 1 on the whole graph, measured in full: BFS
+    levels and the cover-edge pass (single-threaded, as the oracle does
+    them) and the count-once intersection over every cover edge with its
+    outer loop shared among all host cores (OpenMP).  Median of `runs`
+    runs.  Returns (seconds, T, description)."""
+    import oracle
+    times, T, parts = [], None, None
+    threads = os.cpu_count() or 1
+    for _ in range(max(1, runs)):
+        t0 = time.perf_counter()
+        L, _ = oracle.bfs_levels(g)
+        t1 = time.perf_counter()
+        nh = oracle.num_cover(g, L)
+        t2 = time.perf_counter()
+        T = oracle.cetc_count_mt(g, L, threads)
+        t3 = time.perf_counter()
+        times.append(t3 - t0)
+        parts = (t1 - t0, t2 - t1, t3 - t2, nh)
+    t = statistics.median(times)
+    desc = (f"oracle Alg. 1 on the whole graph, measured in full (median of {len(times)} "
+            f"run(s)): BFS {parts[0]:.2f} s and cover-edge pass {parts[1]:.2f} s on one "
+            f"thread, count-once intersection of all {parts[3]} cover edges {parts[2]:.2f} s "
+            f"on {threads} threads (OpenMP)")
+    return t, T, desc
 
 
 # ---------------------------------------------------------------- arms
@@ -293,55 +356,131 @@ def oracle_graph_sample(gs, target_s: float, seed: int = 0):
                         f"single thread")
 
 
+def golden_large():
+    """Oracle results for the benchmark-size graphs, written by
+    tests/golden/make_golden_large.py (which calls only the oracle)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "tests", "golden", "large_counts.json")))
+    except Exception:
+        return {}
+
+
+GOLDEN_NAME = {"rmat22": "rmat_s22", "rmat26": "rmat_s26", "chunglu23": "chung_lu_2_23"}
+
+
+def single_graph_config(g, desc, num_cover, nlevels, max_degree, triangles, world):
+    """The `config` object of a single-graph workload (the same keys and
+    values in both arms)."""
+    csr_bytes = 8 * (g.n + 1) + 4 * g.nnz
+    return {"workload": desc, "n": g.n, "num_edges": g.num_edges, "nnz": g.nnz,
+            "generated_edges": g.generated_edges, "num_cover": int(num_cover),
+            "k_cover_fraction": int(num_cover) / max(g.num_edges, 1),
+            "nlevels": int(nlevels), "max_degree": int(max_degree),
+            "triangles": None if triangles is None else int(triangles),
+            "parallelism": f"independent graphs x{world}",
+            "l2": f"inputs larger than L2 (CSR {csr_bytes / 1e9:.2f} GB > 129 MB)"}
+
+
+def oracle_counts_threads(g, L, uv, threads):
+    """Per-edge Alg. 1 counts of the edge list uv, split among host threads
+    (each thread runs the oracle's single-threaded per-edge function on its
+    share; ctypes releases the interpreter lock during the call)."""
+    import numpy as np
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    parts = np.array_split(np.arange(len(uv)), threads * 8)
+    with ThreadPoolExecutor(threads) as ex:
+        outs = list(ex.map(lambda ix: oracle.cetc_edge_counts(g, L, uv[ix]), parts))
+    return np.concatenate(outs) if outs else np.zeros(0, dtype=np.uint32)
+
+
 def run_reference(args, world, rank):
+    """The oracle as the reference arm, on this arm's workload, config,
+    metric and unit.  Each step is a bounded sample of the workload and
+    ms_per_step is the time the steps actually took."""
     if rank != 0:
         return
+    import numpy as np
+    threads = os.cpu_count() or 1
     if args.workload in ("batch", "serve"):
-        # the oracle over a sample of the workload's graphs, one at a time
+        # one step = the oracle counting a fixed-size random sample of the
+        # workload's graphs, one graph per host thread; value = the sample's
+        # edges / the step's time
         import graphgen as gg
-        specs = gg.mixed_graph_specs(4096, seed=3 if args.workload == "batch" else 11)
-        gs = [gg.graph_from_spec(sp) for sp in specs[:512]]
-        rates, sample_desc = [], ""
-        for i in range(args.warmup + args.steps):
-            r, sample_desc = oracle_graph_sample(gs, target_s=2.0, seed=i)
-            if i >= args.warmup:
-                rates.append(r)
-        value = statistics.mean(rates)
-        desc = ("mixed graphs (R-MAT s6-14 ef8-32 / ER n256-4096 p=10/(n-1) / K20-K200), "
-                f"seed {3 if args.workload == 'batch' else 11}; the oracle counts them one at "
-                "a time")
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        seed = 3 if args.workload == "batch" else 11
+        specs = gg.mixed_graph_specs(4096, seed=seed)
+        rng = np.random.default_rng(seed)
+        per_step = 128
+        times, edges = [], []
+        with ThreadPoolExecutor(threads) as ex:
+            for i in range(args.warmup + args.steps):
+                pick = rng.choice(len(specs), size=per_step, replace=False)
+                gs = list(ex.map(gg.graph_from_spec, [specs[k] for k in pick]))
+                t0 = time.perf_counter()
+                list(ex.map(oracle.cetc, gs))
+                dt = time.perf_counter() - t0
+                if i >= args.warmup:
+                    times.append(dt)
+                    edges.append(sum(g.num_edges for g in gs))
+        value = sum(edges) / sum(times)
+        sample = (f"each step: the oracle's Alg. 1 (BFS, cover edges, count) on {per_step} "
+                  f"graphs drawn at random from the 4,096-graph recipe (seed {seed}), one graph "
+                  f"per host thread ({threads} threads); value = sampled edges / time")
         line = {
             "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            # one step = the 4,096 graphs, estimated from the sampled rate
-            "ms_per_step": 1e3 * 4096 * statistics.mean(g.num_edges for g in gs) / value,
-            "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": desc},
-            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": sample_desc, **cpu_info()},
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": BATCH_DESC if args.workload == "batch" else
+                       serve_desc(args)},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": threads,
+                             "kind": "oracle", "sample": sample, **cpu_info()},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
         }
         print(json.dumps(line), flush=True)
         return
+    import oracle
     g, desc = make_graph(args.workload, 0)
-    times = []
-    sample_desc = ""
+    # setup (untimed): the cover edges to draw each step's sample from
+    L0, nl = oracle.bfs_levels(g)
+    H = oracle.cover_edges(g, L0)
+    h = len(H)
+    frac = 1.0 / max(1, args.ref_sample_div)
+    k = max(1, min(h, int(h * frac)))
+    rng = np.random.default_rng(0)
+    steps, rates = [], []
     for i in range(args.warmup + args.steps):
-        est, sample_desc = oracle_sample(g, target_s=3.0, seed=i)
+        idx = np.sort(rng.choice(h, size=k, replace=False)) if h else np.zeros(0, dtype=np.int64)
+        t0 = time.perf_counter()
+        L, _ = oracle.bfs_levels(g)
+        t1 = time.perf_counter()
+        oracle.num_cover(g, L)
+        t2 = time.perf_counter()
+        if k and h:
+            oracle_counts_threads(g, L, H[idx], threads)
+        t3 = time.perf_counter()
         if i >= args.warmup:
-            times.append(est)
-    t = statistics.mean(times)
-    value = g.num_edges / t
+            steps.append(t3 - t0)
+            est = (t1 - t0) + (t2 - t1) + (t3 - t2) * h / max(k, 1)
+            rates.append(g.num_edges / est)
+    value = statistics.mean(rates)
+    gold = golden_large().get(GOLDEN_NAME.get(args.workload, ""), {})
+    sample = (f"each step: the oracle's BFS and cover-edge pass over the whole graph (one "
+              f"thread) and its count-once intersection of a uniform random 1/"
+              f"{args.ref_sample_div} of the {h} cover edges ({k} edges, {threads} threads); "
+              f"value = |E| / (BFS + cover pass + intersection time x {h}/{k}), an estimate "
+              f"of the full pipeline; ms_per_step = the time each step took")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "n": g.n, "num_edges": g.num_edges},
-        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                         "sample": sample_desc, **cpu_info()},
+        "ms_per_step": 1e3 * statistics.mean(steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": single_graph_config(g, desc, h, nl, g.degrees().max(), gold.get("T"), world),
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": threads, "kind": "oracle",
+                         "sample": sample, **cpu_info()},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -393,11 +532,13 @@ def run_ours(args, world, rank, local):
 
     if args.arm != "all":
         mode = tc.TC_MODE_COVER if args.arm == "cover" else tc.TC_MODE_PLAIN
+        if args.intersect == "merge":
+            mode |= tc.TC_INTERSECT_MERGE
         ms, res, launches = timed(mode)
         if rank == 0:
-            print(json.dumps({"arm": args.arm, "ms_per_step": ms, "triangles": res[0][0],
-                              "stats": res[0][1], "gpu_launches": launches,
-                              "workload": desc}), flush=True)
+            print(json.dumps({"arm": args.arm, "intersect": args.intersect, "ms_per_step": ms,
+                              "triangles": res[0][0], "stats": res[0][1],
+                              "gpu_launches": launches, "workload": desc}), flush=True)
         return
 
     sampler = ClockSampler(gpu_uuid(torch, dev))
@@ -447,22 +588,24 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, sdesc = oracle_sample(g, args.cpu_seconds)
-        cpu = {"value": g.num_edges / est, "unit": "edges/s", "cores": 1, "kind": "oracle",
-               "sample": sdesc, **cpu_info()}
+        t_or, T_or, sdesc = oracle_full_all_cores(g, args.cpu_runs)
+        assert T_or == T, f"oracle T {T_or} != GPU T {T}"
+        cpu = {"value": g.num_edges / t_or, "unit": "edges/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": sdesc, "seconds": t_or, "equals_gpu_count": True,
+               **cpu_info()}
 
     csr_bytes = 8 * (g.n + 1) + 4 * g.nnz
+    dram_frac = None
+    if tr:
+        dram_gbs = tr["bytes_per_launch"] / (ms_k / 1e3) / 1e9
+        dram_frac = dram_gbs / peak
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_cover_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": desc, "n": g.n, "num_edges": g.num_edges, "nnz": g.nnz,
-                   "generated_edges": g.generated_edges, "num_cover": info0["num_cover"],
-                   "k_cover_fraction": info0["num_cover"] / max(g.num_edges, 1),
-                   "nlevels": info0["nlevels"], "max_degree": info0["max_degree"],
-                   "triangles": T, "parallelism": f"independent graphs x{world}",
-                   "l2": f"inputs larger than L2 (CSR {csr_bytes / 1e9:.2f} GB > 129 MB)"},
+        "config": single_graph_config(g, desc, info0["num_cover"], info0["nlevels"],
+                                      info0["max_degree"], T, world),
         "stages_ms": stages,
         "plain": {"value": units / (ms_plain_max / 1e3), "unit": "edges/s",
                   "ms_per_step": ms_plain_max, "stages_ms": stages_plain,
@@ -470,24 +613,66 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": units / (ms_e2e_max / 1e3), "unit": "edges/s",
                 "ms_per_step": ms_e2e_max, "h2d_bytes_per_step": csr_bytes,
                 "d2h_bytes_per_step": 8},
+        # achieved: the kernel's algorithmic bytes (4 per looked-up element
+        # + 72 per edge) over its CUDA-event time; dram_frac: the ncu DRAM
+        # bytes of the same launches (when the capture is of this source)
+        # over the same time; merge_equivalent: the bytes a merge of both
+        # full lists per edge would stream (an effective figure, not a bound)
         "roofline": {"bound": "hbm", "kernel": "k_hash_intersect<cover>", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "frac_of_8tbs_nominal": achieved / 8000.0,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": ms_k,
                      "list_elems": st0["list_elems"],
-                     "merge_equivalent_bytes": merge_bytes,
                      "traffic": tr["bytes_per_launch"] if tr else None,
-                     "traffic_source": tr.get("source") if tr else None},
+                     "traffic_source": tr.get("source") if tr else None,
+                     "dram_frac": dram_frac,
+                     "merge_equivalent_bytes": merge_bytes,
+                     "merge_equivalent_GBps": merge_bytes / (ms_k / 1e3) / 1e9},
         "gpu_launches": launches,
         "clocks": clocks,
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if args.workload == "rmat22" and world == 1:
+        # the batched and serving configurations of the same metric, measured
+        # in the same run on the same GPU
+        del off_d, cols_d, off_h, cols_h
+        torch.cuda.empty_cache()
+        if not args.no_batch:
+            b = measure_batch(args, world, rank, local)
+            line["batch"] = {"workload": b["config"]["workload"],
+                             "ms_per_call": b["ms_per_step"], "value": b["value"],
+                             "unit": "edges/s", "graphs": b["config"]["graphs"],
+                             "looped_plain_ms": b["looped_plain"]["ms_per_step"],
+                             "speedup_vs_looped_plain": b["looped_plain"]["batched_speedup"],
+                             "e2e": b["e2e"], "gpu_launches": b["gpu_launches"],
+                             "options": b["config"]["options"]}
+        if not args.no_serve:
+            sv = measure_serve(args, world, rank, local)
+            line["serve"] = {"workload": sv["config"]["workload"], **sv["serve"],
+                             "offered_req_per_s": sv["config"]["offered_req_per_s"],
+                             "value": sv["value"], "unit": "edges/s",
+                             "fifo_plain": sv["fifo_plain"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
+BATCH_DESC = ("mixed batch of 4096 graphs (R-MAT s6-14 ef8-32 / ER n256-4096 p=10/(n-1) / "
+              "K20-K200, seed 3), one batched launch")
+
+
+def serve_desc(args):
+    return (f"serving: resident R-MAT scale {args.serve_scale} + Poisson stream of "
+            f"{args.requests} requests at {args.rate:g} req/s (seed 11)")
+
+
 def run_batch(args, world, rank, local):
+    line = measure_batch(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_batch(args, world, rank, local):
     """The mixed small-graph batch (4,096 graphs: R-MAT scale 6-14 with
     edgefactor 8-32, Erdos-Renyi G(n, 10/(n-1)) with n in 256-4096, complete
     graphs K_20..K_200; seed 3): one batched cover-edge launch per step
@@ -553,8 +738,7 @@ def run_batch(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "mixed batch of 4096 graphs (R-MAT s6-14 ef8-32 / ER n256-4096 "
-                               "p=10/(n-1) / K20-K200, seed 3), one batched launch",
+        "config": {"workload": BATCH_DESC,
                    "graphs": len(gs), "num_edges": int(units), "triangles": int(outs_b[0].sum()),
                    "options": ({"block_threads": opt.block_threads,
                                 "blocks_per_sm": opt.blocks_per_sm, "skew": opt.skew,
@@ -566,11 +750,16 @@ def run_batch(args, world, rank, local):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12 * len(gs)},
         "gpu_launches": launches,
     }
+    return line
+
+
+def run_serve(args, world, rank, local):
+    line = measure_serve(args, world, rank, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_serve(args, world, rank, local):
+def measure_serve(args, world, rank, local):
     """Serving: a resident R-MAT scale 26 graph (relabel seed 5) and an
     open-loop Poisson stream of requests (seed 11) drawn like the mixed
     batch with 5% R-MAT scale 18-22; latency = scheduled arrival -> poll sees
@@ -590,11 +779,15 @@ def run_serve(args, world, rank, local):
     torch.cuda.set_device(dev)
     nreq, rate = args.requests, args.rate
     rng = random.Random(11)
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    threads = os.cpu_count() or 4
     big = gg.rmat(args.serve_scale, 16, 5, relabel_seed=5 + 2**32)
     small_specs = gg.mixed_graph_specs(2000, seed=11)
-    pool_small = [gg.graph_from_spec(s) for s in small_specs]
-    pool_large = [gg.rmat(sc, 16, 1000 + 10 * sc + k, relabel_seed=2000 + 10 * sc + k)
-                  for sc in range(18, 23) for k in range(2)]
+    large_specs = gg.serve_large_specs()
+    with ThreadPoolExecutor(threads) as ex:
+        pool_small = list(ex.map(gg.graph_from_spec, small_specs))
+        pool_large = list(ex.map(gg.graph_from_spec, large_specs))
     # request mix: request 0 is the resident graph; then 5% large, the rest
     # drawn from the small pool (which already has the 84/10/1 mix)
     reqs = [("resident", None)]
@@ -608,12 +801,26 @@ def run_serve(args, world, rank, local):
     def graph_of(kind, i):
         return big if kind == "resident" else (pool_large[i] if kind == "large" else pool_small[i])
 
-    # expected counts: every distinct graph counted alone
+    # expected counts: every distinct graph counted alone on the GPU, and
+    # the oracle's counts (small graphs: counted here, one graph per host
+    # thread; large ones and the resident graph: the oracle-written golden
+    # file, when it holds them)
     alone = {}
     for kind, pool in (("small", pool_small), ("large", pool_large)):
         for i, g in enumerate(pool):
             with tc.Graph(g.offsets, g.cols) as G:
                 alone[(kind, i)] = G.count(tc.TC_MODE_COVER)
+    with ThreadPoolExecutor(threads) as ex:
+        oracle_small = list(ex.map(lambda g: oracle.cetc(g)["T"], pool_small))
+    gold = golden_large()
+    oracle_T = {("small", i): t for i, t in enumerate(oracle_small)}
+    for i, sp in enumerate(large_specs):
+        e = gold.get("serve_rmat_s{scale}_seed{seed}".format(**sp))
+        if e and e["nnz"] == pool_large[i].nnz:
+            oracle_T[("large", i)] = e["T"]
+    e = gold.get(f"rmat_s{args.serve_scale}")
+    if e and e["nnz"] == big.nnz:
+        oracle_T[("resident", None)] = e["T"]
     units = [graph_of(k, i).num_edges for k, i in reqs]
 
     # ---- served, continuous batching
@@ -674,6 +881,8 @@ def run_serve(args, world, rank, local):
     ok = all(result[i][1] == tc.TC_OK for i in range(nreq))
     same = all(result[i][0] == (resident_T if reqs[i][0] == "resident" else alone[reqs[i]])
                for i in range(nreq))
+    checked = [i for i in range(nreq) if reqs[i] in oracle_T]
+    equals_oracle = all(result[i][0] == oracle_T[reqs[i]] for i in checked)
 
     # ---- baseline: one at a time, FIFO, plain count
     base_done = [0.0] * nreq
@@ -702,13 +911,13 @@ def run_serve(args, world, rank, local):
         "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": (t_end - t0) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": f"serving: resident R-MAT scale {args.serve_scale} + Poisson "
-                               f"stream of {nreq} requests at {rate:g} req/s (seed 11)",
+        "config": {"workload": serve_desc(args),
                    "requests": nreq, "offered_req_per_s": rate,
                    "resident_edges": big.num_edges, "resident_triangles": resident_T},
         "serve": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": float(lat.max()),
                   "achieved_req_per_s": nreq / (t_end - t0), "all_ok": ok,
-                  "each_equals_alone": same,
+                  "each_equals_alone": same, "equals_oracle": equals_oracle,
+                  "oracle_checked_requests": len(checked),
                   "submit_lag_ms": {"p50": pct(np.array(submit_lag) * 1e3, 50),
                                     "max": float(max(submit_lag)) * 1e3},
                   "small_p50_ms": pct(lat[[k for k in range(nreq) if reqs[k][0] == "small"]], 50),
@@ -718,8 +927,7 @@ def run_serve(args, world, rank, local):
                        "achieved_req_per_s": nreq / (b_end - b0),
                        "value": sum(units) / (b_end - b0)},
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_kstudy(args, world, rank):
@@ -759,10 +967,15 @@ def run_kstudy(args, world, rank):
         log_d = comm.clog2(max(nl, 2))
         ours = comm.comm_cetc_bits(g.n, m, h_max / m, 128, log_d) / 8
         prev = comm.wedge_check_bits(wedges, g.n) / 8
+        # Comm-CETC's volume counted on 128 virtual processors (the BFS's
+        # cut edge traversals, the cover-edge exchange, the reduction)
+        meas = comm.measured_volume(g.offsets, g.cols, h_max, nl, 128)
         rows.append({"scale": scale, "n": g.n, "edges": m, "levels": nl,
                      "k_max_degree_root": h_max / m, "k_random_root": h_rand / m,
                      "levels_random_root": nl_r, "k_fit": comm.k_fit(scale),
                      "wedges": wedges, "comm_cetc_bytes_p128": ours,
+                     "comm_cetc_measured_bytes_p128": meas["measured_bits"] / 8,
+                     "bfs_cut_fraction_p128": meas["cut_directed_traversals"] / max(g.nnz, 1),
                      "wedge_check_bytes": prev, "reduction_p128": prev / ours})
         del off, cols
     print(json.dumps({"study": "cover-edge fraction k vs R-MAT scale (edgefactor 16, "
@@ -770,10 +983,80 @@ def run_kstudy(args, world, rank):
                       "fit": "k = 1.1773 exp(-0.036 scale)", "rows": rows}), flush=True)
 
 
+def shard_steps(make_graph_obj, mode, steps, warmup, rank, world, all_reduce, sync, clock):
+    """The sharded step loop: every step builds the rank's graph object
+    (levels and cover edges are computed inside it, the same on every rank),
+    takes its work-balanced slice (tc_shard_bounds), counts it
+    (tc_count_range) and sums the slice counts with one all-reduce.  Returns
+    (per-step seconds of the timed steps, the totals).  `sync()` is a
+    barrier plus a device synchronisation; `clock()` a host timer."""
+    from paper_2210_00389_gb300.shard import count_sharded
+
+    def one():
+        with make_graph_obj() as G:
+            return count_sharded(G, mode, rank, world, all_reduce)[1]
+
+    for _ in range(warmup):
+        one()
+    sync()
+    t0 = clock()
+    totals = [one() for _ in range(steps)]
+    sync()
+    return (clock() - t0) / max(steps, 1), totals
+
+
+def run_shard(args, world, rank, local):
+    """One graph counted by all ranks (strong scaling): edge-range shards of
+    the cover edges, one int64 all-reduce per step (NCCL)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2210_00389_gb300 as tc
+    from paper_2210_00389_gb300.shard import torch_all_reduce_sum
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    g, desc = make_graph(args.workload, 0)  # the same graph on every rank
+    off_d = torch.from_numpy(g.offsets).to(dev)
+    cols_d = torch.from_numpy(g.cols).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+
+    def sync():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = tc.tc_kernel_launches()
+    sec, totals = shard_steps(
+        lambda: tc.Graph(off_d, cols_d, g.n, tc.TC_GRAPH_BORROW | tc.TC_GRAPH_VALIDATE, stream),
+        tc.TC_MODE_COVER, args.steps, args.warmup, rank, world, torch_all_reduce_sum(dev),
+        sync, time.perf_counter)
+    launches = tc.tc_kernel_launches() - launches0
+    assert len(set(totals)) == 1
+    sec = reduce_max(sec, world, dev)
+    line = {
+        "metric": METRIC, "value": g.num_edges / sec, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": desc, "n": g.n, "num_edges": g.num_edges, "nnz": g.nnz,
+                   "triangles": int(totals[0]),
+                   "parallelism": f"edge-range shards of H x{world}, one int64 all-reduce",
+                   "timing": "host clock around the steps, barrier + device sync on both sides"},
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_init()
-    if args.workload == "serve" and args.impl == "ours":
+    shard = args.shard if args.shard is not None else (world > 1)
+    if args.impl == "ours" and shard and args.workload in ("rmat22", "rmat26", "chunglu23",
+                                                           "rmat18", "rmat20"):
+        run_shard(args, world, rank, local)
+    elif args.workload == "serve" and args.impl == "ours":
         run_serve(args, world, rank, local)
     elif args.workload == "batch" and args.impl == "ours":
         run_batch(args, world, rank, local)

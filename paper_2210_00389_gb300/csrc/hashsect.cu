@@ -27,9 +27,9 @@
 // Bucketing (a3) is a counting sort of the edges by owner.  Owners of degree
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
 // split into work items (owner, slot) of about item_work lookups; a CTA
-// takes an item, builds a bucketized hash table of N(o) in shared memory
-// (the CTA's whole table, in buckets of kSlots slots, load <= 1/2; usually
-// one shared load per lookup) and its warps take the item's edges from a
+// takes an item, builds a two-choice (cuckoo) hash table of N(o) in shared
+// memory (the CTA's whole table, at most 1/3 full; two independent 4-byte
+// shared loads per lookup) and its warps take the item's edges from a
 // shared counter.
 // Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (five
 // per SM); larger owners use 1024-thread CTAs with 224 KB tables.  Rows
@@ -318,61 +318,44 @@ __global__ void k_u32_to_u64(const uint32_t* __restrict__ a, uint32_t n, unsigne
 
 // ------------------------------------------------------------------ hashing
 
-// Bucket of w among nb buckets: multiply-high of a Fibonacci hash (Knuth's
-// multiplicative hashing with 2^32/phi; Lemire's multiply-shift range map),
-// so nb need not be a power of two.
-__device__ __forceinline__ uint32_t hash_bucket(uint32_t w, uint32_t nb) {
-  return __umulhi(w * 0x9E3779B1u, nb);
+// Two-choice (cuckoo) table of 2 nh 4-byte slots in shared memory: key w
+// lives either in slot h1(w) of the first half or in slot nh + h2(w) of the
+// second (Pagh and Rodler's cuckoo hashing, two tables).  A lookup reads
+// both slots -- two independent 4-byte shared loads, two compares, no
+// probe loop -- so it holds three registers per key in flight, and a warp's
+// reads of 32 random words cost far fewer shared-memory wavefronts than 16-
+// byte bucket reads.  h1, h2: multiply-high of two multiplicative hashes
+// (Knuth's 2^32/phi and another odd constant; Lemire's range map), so nh
+// need not be a power of two.
+__device__ __forceinline__ uint32_t slot1(uint32_t w, uint32_t nh) {
+  return __umulhi(w * 0x9E3779B1u, nh);
+}
+__device__ __forceinline__ uint32_t slot2(uint32_t w, uint32_t nh) {
+  return nh + __umulhi(w * 0x85EBCA77u, nh);
 }
 
-__device__ __forceinline__ uint32_t next_bucket(uint32_t b, uint32_t nb) {
-  return b + 1 == nb ? 0u : b + 1;
-}
+// Insertion moves keys between their two slots (atomicExch chains, any
+// number of threads at once: every key is always in the table or held by
+// exactly one thread).  A chain longer than kMaxKicks gives up and returns
+// false: the key it holds is lost, and the caller rebuilds the table with a
+// smaller window.  At the loads used here (at most 1/3 of the slots) that
+// is very rare; a window of one key always fits.
+constexpr int kMaxKicks = 64;
 
-// Buckets of kSlots 4-byte slots (one 16-, 8- or 4-byte shared load each).
-// The table always has 4 slots per entry (load <= 1/4), so narrower buckets
-// mean more of them: fewer bytes per lookup and fewer bank conflicts, at
-// the price of more overflow into the next bucket.
-constexpr int kSlots = 4;
-template <int S> struct BucketOf;
-template <> struct BucketOf<4> {
-  using T = uint4;
-  __device__ static T none() { return make_uint4(kEmpty, kEmpty, kEmpty, kEmpty); }
-  __device__ static bool has(T q, uint32_t w) { return q.x == w || q.y == w || q.z == w || q.w == w; }
-  __device__ static uint32_t last(T q) { return q.w; }
-};
-template <> struct BucketOf<2> {
-  using T = uint2;
-  __device__ static T none() { return make_uint2(kEmpty, kEmpty); }
-  __device__ static bool has(T q, uint32_t w) { return q.x == w || q.y == w; }
-  __device__ static uint32_t last(T q) { return q.y; }
-};
-template <> struct BucketOf<1> {
-  using T = uint32_t;
-  __device__ static T none() { return kEmpty; }
-  __device__ static bool has(T q, uint32_t w) { return q == w; }
-  __device__ static uint32_t last(T q) { return q; }
-};
-using Bucket = BucketOf<kSlots>;
-using BucketT = Bucket::T;
-
-__device__ __forceinline__ void table_insert(uint32_t* tab, uint32_t nb, uint32_t w) {
-  uint32_t b = hash_bucket(w, nb);
-  while (true) {
-#pragma unroll
-    for (int k = 0; k < kSlots; ++k)
-      if (atomicCAS(&tab[kSlots * b + k], kEmpty, w) == kEmpty) return;
-    b = next_bucket(b, nb);
+__device__ __forceinline__ bool table_insert(uint32_t* tab, uint32_t nh, uint32_t w) {
+  uint32_t pos = slot1(w, nh);
+  for (int it = 0; it < kMaxKicks; ++it) {
+    const uint32_t old = atomicExch(&tab[pos], w);
+    if (old == kEmpty) return true;
+    w = old;  // the displaced key moves to its other slot
+    pos = pos < nh ? slot2(w, nh) : slot1(w, nh);
   }
+  return false;
 }
 
-// Slots of a bucket fill in order and never empty again, so a bucket whose
-// last slot is empty ends the search.
 // Warp-uniform: all 32 lanes call it, each with U keys (valid[j] = false on
-// padding).  The U first bucket reads are issued together (lanes with an
-// invalid key read nothing); a key whose bucket is full without a match
-// moves to the next bucket, and that loop runs only while some key of some
-// lane still needs one.  Returns the lane's hits; sink(w) is called on each
+// padding: such a key reads nothing and never hits).  All 2U slot reads are
+// issued together.  Returns the lane's hits; sink(w) is called on each
 // (NoSink: nothing, for the counts).
 struct NoSink {
   __device__ __forceinline__ void operator()(uint32_t) const {}
@@ -385,39 +368,22 @@ struct ApexSink {
 };
 
 template <int U, class Sink = NoSink>
-__device__ __forceinline__ unsigned table_find_n(const BucketT* tab, uint32_t nb,
+__device__ __forceinline__ unsigned table_find_n(const uint32_t* tab, uint32_t nh,
                                                  const uint32_t (&w)[U], const bool (&valid)[U],
                                                  Sink sink = Sink()) {
-  uint32_t b[U];
-  BucketT q[U];
-#pragma unroll
-  for (int j = 0; j < U; ++j) b[j] = hash_bucket(w[j], nb);
-#pragma unroll
-  for (int j = 0; j < U; ++j) q[j] = valid[j] ? tab[b[j]] : Bucket::none();
-  bool hit[U], more[U];
-  bool any = false;
+  uint32_t a[U], b[U];
 #pragma unroll
   for (int j = 0; j < U; ++j) {
-    hit[j] = valid[j] && Bucket::has(q[j], w[j]);
-    more[j] = valid[j] && !hit[j] && Bucket::last(q[j]) != kEmpty;
-    any |= more[j];
+    a[j] = valid[j] ? tab[slot1(w[j], nh)] : kEmpty;
+    b[j] = valid[j] ? tab[slot2(w[j], nh)] : kEmpty;
   }
-  while (__any_sync(0xFFFFFFFFu, any)) {
-    any = false;
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      if (more[j]) {
-        b[j] = next_bucket(b[j], nb);
-        const BucketT r = tab[b[j]];
-        hit[j] = Bucket::has(r, w[j]);
-        more[j] = !hit[j] && Bucket::last(r) != kEmpty;
-        any |= more[j];
-      }
-    }
-  }
+  bool hit[U];
   unsigned c = 0;
 #pragma unroll
-  for (int j = 0; j < U; ++j) c += hit[j] ? 1u : 0u;
+  for (int j = 0; j < U; ++j) {
+    hit[j] = valid[j] && (a[j] == w[j] || b[j] == w[j]);
+    c += hit[j] ? 1u : 0u;
+  }
 #pragma unroll
   for (int j = 0; j < U; ++j)
     if (hit[j]) sink(w[j]);
@@ -437,7 +403,7 @@ constexpr uint32_t kGroup = 32 * kUnroll;  // probe elements a warp looks up at 
 // validity tests are executed.
 template <class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict__ P,
-                                                     const BucketT* tab, uint32_t nb,
+                                                     const uint32_t* tab, uint32_t nh,
                                                      Sink sink = Sink()) {
   const int lane = threadIdx.x & 31;
   uint32_t w[kUnroll];
@@ -447,7 +413,7 @@ __device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict_
     w[j] = __ldg(P + j * 32 + lane);
     ok[j] = true;
   }
-  return table_find_n<kUnroll>(tab, nb, w, ok, sink);
+  return table_find_n<kUnroll>(tab, nh, w, ok, sink);
 }
 
 // U rounds of the remainder index space [0, tt) from k0: element k is
@@ -457,7 +423,7 @@ __device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ R0,
                                                const uint32_t* __restrict__ R1,
                                                const uint32_t* __restrict__ R2, uint32_t s1,
                                                uint32_t s2, uint32_t tt, uint32_t k0,
-                                               const BucketT* tab, uint32_t nb,
+                                               const uint32_t* tab, uint32_t nh,
                                                Sink sink = Sink()) {
   const int lane = threadIdx.x & 31;
   uint32_t w[U];
@@ -468,7 +434,7 @@ __device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ R0,
     ok[j] = k < tt;
     w[j] = ok[j] ? __ldg((k < s1 ? R0 : (k < s2 ? R1 : R2)) + k) : kEmpty;
   }
-  return table_find_n<U>(tab, nb, w, ok, sink);
+  return table_find_n<U>(tab, nh, w, ok, sink);
 }
 
 // Look up every element of up to three ranges Q[i][0, m[i]): the full
@@ -480,7 +446,7 @@ template <class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0,
                                                  const uint32_t* Q1, uint32_t m1,
                                                  const uint32_t* Q2, uint32_t m2,
-                                                 const BucketT* tab, uint32_t nb,
+                                                 const uint32_t* tab, uint32_t nh,
                                                  Sink sink = Sink()) {
   const uint32_t g0 = m0 / kGroup, g1 = m1 / kGroup, g2 = m2 / kGroup;
   const uint32_t g01 = g0 + g1, ng = g01 + g2;
@@ -504,11 +470,11 @@ __device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0
       const uint32_t* gp = group_ptr(g);
 #pragma unroll
       for (int j = 0; j < kUnroll; ++j) nxt[j] = __ldg(gp + j * 32 + lane);
-      c += table_find_n<kUnroll>(tab, nb, cur, ok, sink);
+      c += table_find_n<kUnroll>(tab, nh, cur, ok, sink);
 #pragma unroll
       for (int j = 0; j < kUnroll; ++j) cur[j] = nxt[j];
     }
-    c += table_find_n<kUnroll>(tab, nb, cur, ok, sink);
+    c += table_find_n<kUnroll>(tab, nh, cur, ok, sink);
   }
   const uint32_t f0 = g0 * kGroup, f1 = g1 * kGroup, f2 = g2 * kGroup;
   const uint32_t r0 = m0 - f0, s1 = r0 + (m1 - f1), tt = s1 + (m2 - f2);
@@ -517,18 +483,18 @@ __device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0
   const uint32_t* R2 = Q2 + f2 - s1;
   uint32_t k0 = 0;
   for (; k0 + 64 < tt; k0 += kGroup)
-    c += probe_tail<kUnroll>(R0, R1, R2, r0, s1, tt, k0, tab, nb, sink);
-  if (k0 + 32 < tt) c += probe_tail<2>(R0, R1, R2, r0, s1, tt, k0, tab, nb, sink);
-  else if (k0 < tt) c += probe_tail<1>(R0, R1, R2, r0, s1, tt, k0, tab, nb, sink);
+    c += probe_tail<kUnroll>(R0, R1, R2, r0, s1, tt, k0, tab, nh, sink);
+  if (k0 + 32 < tt) c += probe_tail<2>(R0, R1, R2, r0, s1, tt, k0, tab, nh, sink);
+  else if (k0 < tt) c += probe_tail<1>(R0, R1, R2, r0, s1, tt, k0, tab, nh, sink);
   return c;
 }
 
 // All probe elements of a descriptor: runs [0, x) and [cut, end) of P.
 template <class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
-                                              const BucketT* tab, uint32_t nb,
+                                              const uint32_t* tab, uint32_t nh,
                                               Sink sink = Sink()) {
-  return probe_ranges(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nb, sink);
+  return probe_ranges(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nh, sink);
 }
 
 // Number of elements <= hi in the sorted run P[a, b), by a 32-ary search
@@ -561,7 +527,7 @@ constexpr uint32_t kBatchMaxWork = 64;  // tasks with fewer lookups share a warp
 // Larger tasks are then done one at a time by the whole warp.
 __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pcols,
                                                 const uint4* __restrict__ descs, uint64_t t0,
-                                                uint32_t nt, const BucketT* tab, uint32_t nb,
+                                                uint32_t nt, const uint32_t* tab, uint32_t nh,
                                                 unsigned long long* probes) {
   const int lane = threadIdx.x & 31;
   const uint4 ds = (uint32_t)lane < nt ? descs[t0 + lane] : make_uint4(0u, 0u, 0u, 0u);
@@ -599,7 +565,7 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
     bool ok[kUnroll];
 #pragma unroll
     for (int j = 0; j < kUnroll; ++j) ok[j] = e[j] != kEmpty;
-    c += table_find_n<kUnroll>(tab, nb, e, ok);
+    c += table_find_n<kUnroll>(tab, nh, e, ok);
   }
   if (lane == 0) *probes += total;
   unsigned big = __ballot_sync(0xFFFFFFFFu, (uint32_t)lane < nt && !small);
@@ -611,7 +577,7 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
     dj.y = __shfl_sync(0xFFFFFFFFu, ds.y, j);
     dj.z = __shfl_sync(0xFFFFFFFFu, ds.z, j);
     dj.w = __shfl_sync(0xFFFFFFFFu, ds.w, j);
-    c += probe_all(pcols + dj.x, dj, tab, nb);
+    c += probe_all(pcols + dj.x, dj, tab, nh);
     if (lane == 0) *probes += desc_work(dj);
   }
   return c;
@@ -620,7 +586,7 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
 // VERT (cover mode only): per-vertex triangle counts instead of per-edge
 // ones -- every hit adds one to its apex, and each edge's count is added to
 // both of its endpoints (H[task_idx[t]]).
-template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH, bool VERT>
+template <int M, int THREADS, int SLOTS, int WIN, int MINB, bool BATCH, bool VERT>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                  const uint32_t* __restrict__ pcols, const uint2* __restrict__ items,
@@ -631,11 +597,12 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  const uint2* __restrict__ H, unsigned long long* __restrict__ tv,
                  unsigned long long* ctrl) {
   constexpr int kWarps = THREADS / 32;
-  constexpr uint32_t kWin = WIN;          // owner entries per table window
-  extern __shared__ uint4 tab4[];         // 4 * BUCKETS slots (dynamic shared memory)
+  constexpr uint32_t kWin = WIN;          // owner entries per table window (at most)
+  constexpr uint32_t kHalf = SLOTS / 2;   // slots per half of the two-choice table
+  extern __shared__ uint4 tab4[];         // SLOTS slots (dynamic shared memory)
   __shared__ unsigned long long s_next;
-  uint32_t* tab32 = reinterpret_cast<uint32_t*>(tab4);
-  const BucketT* tab = reinterpret_cast<const BucketT*>(tab4);
+  __shared__ int s_fail;
+  uint32_t* tab = reinterpret_cast<uint32_t*>(tab4);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long acc = 0, probes = 0;
   // one item per CTA (grid-stride only beyond the grid limit): CTAs end
@@ -647,24 +614,32 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
     const uint64_t ta = T0 + T * slot / nsl, tb = T0 + T * (slot + 1) / nsl;
     const int64_t ro = off[o];
     const uint32_t d = (uint32_t)(off[o + 1] - ro);
-    const uint32_t nwin = (d + kWin - 1) / kWin;
-    // the whole table (4 * BUCKETS slots) even for a short row: a lower
-    // load means fewer lookups that overflow into a second bucket, and every
-    // overflow costs the warp another round
-    const uint32_t nq = (uint32_t)BUCKETS;
-    const uint32_t nb = nq * (4 / kSlots);
-    for (uint32_t wdx = 0; wdx < nwin; ++wdx) {
-      const uint32_t wb = wdx * kWin;
-      const uint32_t we = min(d, wb + kWin);
-      const uint32_t hi = (wdx + 1 == nwin) ? kEmpty - 1u : cols[ro + we - 1];
-      for (uint32_t k = threadIdx.x; k < nq; k += THREADS)
-        tab4[k] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-      if (threadIdx.x == 0) s_next = ta;
-      __syncthreads();
-      for (uint32_t k = wb + threadIdx.x; k < we; k += THREADS)
-        table_insert(tab32, nb, cols[ro + k]);
-      __syncthreads();
-      if (BATCH && nwin == 1 && per_edge == nullptr) {
+    // windows of consecutive entries of N(o) (an id range each), at most
+    // kWin long; a window whose table cannot be built is halved
+    for (uint32_t wb = 0; wb < d;) {
+      uint32_t we = min(d, wb + kWin);
+      while (true) {
+        for (uint32_t k = threadIdx.x; k < SLOTS / 4; k += THREADS)
+          tab4[k] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+        if (threadIdx.x == 0) {
+          s_next = ta;
+          s_fail = 0;
+        }
+        __syncthreads();
+        bool ok = true;
+        for (uint32_t k = wb + threadIdx.x; k < we; k += THREADS)
+          ok &= table_insert(tab, kHalf, cols[ro + k]);
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        // a one-key window always fits (its first slot is empty), so the
+        // second test only bounds the loop
+        if (!s_fail || we - wb <= 1) break;
+        we = wb + (we - wb) / 2;
+        __syncthreads();  // every thread has read s_fail before it is reset
+      }
+      const bool whole = wb == 0 && we == d;
+      const uint32_t hi = we == d ? kEmpty - 1u : cols[ro + we - 1];
+      if (BATCH && whole && per_edge == nullptr) {
         // warps take 32 edges at a time and share passes over short lists
         while (true) {
           unsigned long long t = 0;
@@ -672,7 +647,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           t = __shfl_sync(0xFFFFFFFFu, t, 0);
           if (t >= tb) break;
           const uint32_t nt = (uint32_t)min((unsigned long long)32, tb - t);
-          acc += probe_batch(pcols, descs, t, nt, tab, nb, &probes);
+          acc += probe_batch(pcols, descs, t, nt, tab, kHalf, &probes);
         }
       } else
       while (true) {
@@ -683,25 +658,26 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         const uint4 ds = descs[t];
         const uint32_t* P = pcols + ds.x;
         unsigned c;
-        if (nwin == 1) {
-          if constexpr (VERT) c = probe_all(P, ds, tab, nb, ApexSink{tv});
-          else c = probe_all(P, ds, tab, nb);
+        if (whole) {
+          if constexpr (VERT) c = probe_all(P, ds, tab, kHalf, ApexSink{tv});
+          else c = probe_all(P, ds, tab, kHalf);
           if (lane == 0) probes += desc_work(ds);
         } else {
           // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
           const uint32_t z = task_split[t];
-          uint4 cur = wdx == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
+          uint4 cur = wb == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
           // this window's elements of each run: the prefix <= hi
           const uint32_t m0 = count_le(P, cur.x, ds.y, hi);
           const uint32_t m1 = count_le(P, cur.y, z, hi);
           const uint32_t m2 = count_le(P, cur.z, ds.w, hi);
           if constexpr (VERT)
-            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, nb, ApexSink{tv});
+            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf,
+                             ApexSink{tv});
           else
-            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, nb);
+            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf);
           if (lane == 0) {
             probes += m0 + m1 + m2;
-            if (wdx + 1 < nwin) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
+            if (we < d) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
           }
         }
         acc += c;
@@ -719,6 +695,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
         }
       }
       __syncthreads();
+      wb = we;
     }
   }
   // block reduction of the count and the lookup total
@@ -740,33 +717,36 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
 }
 
 // Table configurations: medium owners (degree <= kMediumMax) in 256-thread
-// CTAs with 32 KB tables, five per SM; large owners in 1024-thread CTAs with
-// 224 KB tables, one per SM.
-constexpr int kMedThreads = 256, kMedBuckets = 2048, kMedPerSM = 5;
-constexpr int kBigThreads = 1024, kBigBuckets = 14336, kBigPerSM = 1;
+// CTAs with 32 KB tables (8,192 slots), five per SM; large owners in
+// 1024-thread CTAs with 224 KB tables (57,344 slots), one per SM.
+constexpr int kMedThreads = 256, kMedSlots = 8192, kMedPerSM = 5;
+constexpr int kBigThreads = 1024, kBigSlots = 57344, kBigPerSM = 1;
 // Owner entries per table window, per mode (cover, plain): every owner row
 // longer than this is processed in windows, and each window pass revisits
-// all the owner's edges, so a larger window (at a higher table load, more
-// lookups overflowing into a second bucket) can pay.  Tuned on R-MAT scale
-// 20 and 22.
-constexpr int kMedWin = kMedBuckets;
+// all the owner's edges.  The two-choice table stays at most 1/3 full
+// (windows of 19,104 measured faster than 14,336 for cover on R-MAT scale
+// 22 and Chung-Lu 2^23).
+constexpr int kMedWin = (int)kMediumMax;
 // Medium owners' edges with fewer than kBatchMaxWork lookups share warp
 // passes (probe_batch) in plain mode, whose upper-neighbour probe lists are
 // often that short; cover probe lists rarely are.  Measured on R-MAT scale
 // 20 and 22.
 constexpr bool kMedBatch[2] = {false, true};
-constexpr int kBigWin[2] = {14336, 28672};
-static_assert(kMedBuckets >= (int)kMediumMax, "medium owners fit one table");
+constexpr int kBigWin[2] = {19104, 19104};
+static_assert(3 * kMedWin <= kMedSlots && 3 * kBigWin[0] <= kBigSlots &&
+                  3 * kBigWin[1] <= kBigSlots,
+              "two-choice tables at most 1/3 full");
+static_assert(kMedSlots % 8 == 0 && kBigSlots % 8 == 0, "tables in whole 16-byte halves");
 
-template <int M, int THREADS, int BUCKETS, int WIN, int MINB, bool BATCH, bool VERT = false>
+template <int M, int THREADS, int SLOTS, int WIN, int MINB, bool BATCH, bool VERT = false>
 static int launch_hash(tc_graph* g, const uint32_t* pcols, const uint2* items, uint64_t nitems,
                        const unsigned long long* ostart, const uint32_t* owner_cnt,
                        const uint4* descs, const uint32_t* task_split, const uint32_t* task_idx,
                        uint4* cursors, uint32_t* per_edge, unsigned long long* tv = nullptr) {
   if (nitems == 0) return TC_OK;
   cudaStream_t st = g->stream;
-  const size_t smem = sizeof(uint4) * BUCKETS;
-  auto k = k_hash_intersect<M, THREADS, BUCKETS, WIN, MINB, BATCH, VERT>;
+  const size_t smem = sizeof(uint32_t) * SLOTS;
+  auto k = k_hash_intersect<M, THREADS, SLOTS, WIN, MINB, BATCH, VERT>;
   TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t grid = std::min<uint64_t>(nitems, 0x7FFFFFFFull);
   launch(k, (unsigned)grid, THREADS, smem, st, g->off, g->cols, pcols, items, nitems, ostart,
@@ -838,10 +818,10 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   cudaEventRecord(g->ev[6], st);  // end of bucketing
   if constexpr (M == kModeCover) {
     if (tv) {
-      TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigWin[M], kBigPerSM, false, true>(
+      TC_TRY((launch_hash<M, kBigThreads, kBigSlots, kBigWin[M], kBigPerSM, false, true>(
           g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
           cursors.p, nullptr, tv)));
-      TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedWin, kMedPerSM, false, true>(
+      TC_TRY((launch_hash<M, kMedThreads, kMedSlots, kMedWin, kMedPerSM, false, true>(
           g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
           cursors.p, nullptr, tv)));
       // the merge list's edges, with a sink per apex (find.cu)
@@ -850,10 +830,10 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
       return TC_OK;
     }
   }
-  TC_TRY((launch_hash<M, kBigThreads, kBigBuckets, kBigWin[M], kBigPerSM, false>(
+  TC_TRY((launch_hash<M, kBigThreads, kBigSlots, kBigWin[M], kBigPerSM, false>(
       g, pcols, items1.p, nitems1, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge)));
-  TC_TRY((launch_hash<M, kMedThreads, kMedBuckets, kMedWin, kMedPerSM, kMedBatch[M]>(
+  TC_TRY((launch_hash<M, kMedThreads, kMedSlots, kMedWin, kMedPerSM, kMedBatch[M]>(
       g, pcols, items0.p, nitems0, ostart.p, owner_cnt.p, descs.p, task_split.p, task_idx.p,
       cursors.p, per_edge)));
   cudaEventRecord(g->ev[7], st);  // end of the hash kernels

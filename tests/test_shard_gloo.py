@@ -31,6 +31,12 @@ class OracleGraph:
     def count_range(self, mode, begin, end):
         return int(self.per[begin:end].sum())
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
 
 def _graph():
     import graphgen as gg
@@ -95,3 +101,44 @@ def test_dead_rank_is_reported():
     out = _run(2, die_rank=1)
     assert out[1][1] == "died"
     assert out[0][1] == "error"            # rank 0's all-reduce failed, no hang
+
+
+def _bench_worker(rank, world, port, q):
+    """bench.py's sharded step loop (the default under torchrun) on gloo
+    ranks, with the oracle-backed graph object in place of the device."""
+    import sys
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2210_00389_gb300.shard import torch_all_reduce_sum
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    per, T = _graph()
+    try:
+        sec, totals = bench.shard_steps(lambda: OracleGraph(per), 0, 3, 2, rank, world,
+                                        torch_all_reduce_sum(), dist.barrier, time.perf_counter)
+        q.put((rank, "ok", sec >= 0, totals == [T] * 3))
+    except Exception as e:  # noqa: BLE001 -- reported to the parent
+        q.put((rank, "error", type(e).__name__, str(e)[:200]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_bench_shard_mode(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    assert [o[1] for o in out] == ["ok"] * world, out
+    assert all(o[2] and o[3] for o in out)

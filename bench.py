@@ -65,9 +65,10 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=20000, help="serve: stream length")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
     ap.add_argument("--serve-scale", type=int, default=26, help="serve: resident R-MAT scale")
-    ap.add_argument("--arm", default="all", choices=["all", "cover", "plain"],
+    ap.add_argument("--arm", default="all", choices=["all", "cover", "plain", "both"],
                     help="'cover' or 'plain' runs only that device-resident arm "
-                         "(for profiling one step); 'all' is the benchmark")
+                         "(for profiling one step), 'both' the two in turn (one line "
+                         "each); 'all' is the benchmark")
     ap.add_argument("--intersect", default="hash", choices=["hash", "merge"],
                     help="with --arm: the owner-grouped hash intersection (the product "
                          "path) or the warp merge / binary-search kernels (Sec. V-A's other "
@@ -531,14 +532,15 @@ def run_ours(args, world, rank, local):
         return ms, res, tc.tc_kernel_launches() - l0
 
     if args.arm != "all":
-        mode = tc.TC_MODE_COVER if args.arm == "cover" else tc.TC_MODE_PLAIN
-        if args.intersect == "merge":
-            mode |= tc.TC_INTERSECT_MERGE
-        ms, res, launches = timed(mode)
-        if rank == 0:
-            print(json.dumps({"arm": args.arm, "intersect": args.intersect, "ms_per_step": ms,
-                              "triangles": res[0][0], "stats": res[0][1],
-                              "gpu_launches": launches, "workload": desc}), flush=True)
+        for arm in (("cover", "plain") if args.arm == "both" else (args.arm,)):
+            mode = tc.TC_MODE_COVER if arm == "cover" else tc.TC_MODE_PLAIN
+            if args.intersect == "merge":
+                mode |= tc.TC_INTERSECT_MERGE
+            ms, res, launches = timed(mode)
+            if rank == 0:
+                print(json.dumps({"arm": arm, "intersect": args.intersect, "ms_per_step": ms,
+                                  "triangles": res[0][0], "stats": res[0][1],
+                                  "gpu_launches": launches, "workload": desc}), flush=True)
         return
 
     sampler = ClockSampler(gpu_uuid(torch, dev))

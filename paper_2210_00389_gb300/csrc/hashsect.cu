@@ -649,49 +649,58 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           const uint32_t nt = (uint32_t)min((unsigned long long)32, tb - t);
           acc += probe_batch(pcols, descs, t, nt, tab, kHalf, &probes);
         }
-      } else
-      while (true) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(&s_next, 1ull);
-        t = __shfl_sync(0xFFFFFFFFu, t, 0);
-        if (t >= tb) break;
-        const uint4 ds = descs[t];
-        const uint32_t* P = pcols + ds.x;
-        unsigned c;
-        if (whole) {
-          if constexpr (VERT) c = probe_all(P, ds, tab, kHalf, ApexSink{tv});
-          else c = probe_all(P, ds, tab, kHalf);
-          if (lane == 0) probes += desc_work(ds);
-        } else {
-          // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
-          const uint32_t z = task_split[t];
-          uint4 cur = wb == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
-          // this window's elements of each run: the prefix <= hi
-          const uint32_t m0 = count_le(P, cur.x, ds.y, hi);
-          const uint32_t m1 = count_le(P, cur.y, z, hi);
-          const uint32_t m2 = count_le(P, cur.z, ds.w, hi);
-          if constexpr (VERT)
-            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf,
-                             ApexSink{tv});
-          else
-            c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf);
-          if (lane == 0) {
-            probes += m0 + m1 + m2;
-            if (we < d) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
+      } else {
+        // each warp holds its next task and that task's descriptor in flight
+        // while it works on the current one
+        auto grab = [&]() {
+          unsigned long long t = 0;
+          if (lane == 0) t = atomicAdd(&s_next, 1ull);
+          return __shfl_sync(0xFFFFFFFFu, t, 0);
+        };
+        unsigned long long t = grab();
+        uint4 ds = t < tb ? descs[t] : make_uint4(0u, 0u, 0u, 0u);
+        while (t < tb) {
+          const unsigned long long tn = grab();
+          const uint4 dn = tn < tb ? descs[tn] : make_uint4(0u, 0u, 0u, 0u);
+          const uint32_t* P = pcols + ds.x;
+          unsigned c;
+          if (whole) {
+            if constexpr (VERT) c = probe_all(P, ds, tab, kHalf, ApexSink{tv});
+            else c = probe_all(P, ds, tab, kHalf);
+            if (lane == 0) probes += desc_work(ds);
+          } else {
+            // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
+            const uint32_t z = task_split[t];
+            uint4 cur = wb == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
+            // this window's elements of each run: the prefix <= hi
+            const uint32_t m0 = count_le(P, cur.x, ds.y, hi);
+            const uint32_t m1 = count_le(P, cur.y, z, hi);
+            const uint32_t m2 = count_le(P, cur.z, ds.w, hi);
+            if constexpr (VERT)
+              c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf,
+                               ApexSink{tv});
+            else
+              c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf);
+            if (lane == 0) {
+              probes += m0 + m1 + m2;
+              if (we < d) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
+            }
           }
-        }
-        acc += c;
-        if (per_edge) {
-          const unsigned long long tsum = warp_sum_u64(c);
-          if (lane == 0 && tsum) atomicAdd(&per_edge[task_idx[t]], (uint32_t)tsum);
-        }
-        if constexpr (VERT) {
-          const unsigned long long tsum = warp_sum_u64(c);
-          if (lane == 0 && tsum) {
-            const uint2 e = H[task_idx[t]];
-            atomicAdd(&tv[e.x], tsum);
-            atomicAdd(&tv[e.y], tsum);
+          acc += c;
+          if (per_edge) {
+            const unsigned long long tsum = warp_sum_u64(c);
+            if (lane == 0 && tsum) atomicAdd(&per_edge[task_idx[t]], (uint32_t)tsum);
           }
+          if constexpr (VERT) {
+            const unsigned long long tsum = warp_sum_u64(c);
+            if (lane == 0 && tsum) {
+              const uint2 e = H[task_idx[t]];
+              atomicAdd(&tv[e.x], tsum);
+              atomicAdd(&tv[e.y], tsum);
+            }
+          }
+          t = tn;
+          ds = dn;
         }
       }
       __syncthreads();

@@ -77,6 +77,14 @@ struct EdgeSrc {
   uint64_t first;  // edge index of local index 0 (a shard's first edge)
 };
 
+// Cover edges on level 1: both endpoints' only lower-level neighbour is
+// their component's root (level 0 holds only roots), so the root is a
+// common neighbour on another level -- one that Alg. 1's predicate counts
+// -- and the level l-1 run needs no lookup.  The descriptor marks such an
+// edge with this bit in its run-0 length (the run itself left empty) and
+// the kernel adds the root's one.
+constexpr uint32_t kRootBonus = 0x80000000u;
+
 // Decode edge `idx`: returns false for plain entries that are not u < v.
 template <int M>
 __device__ __forceinline__ bool edge_at(const EdgeSrc& s, uint64_t idx, uint32_t& u, uint32_t& v) {
@@ -116,14 +124,17 @@ __device__ __forceinline__ uint4 probe_desc(const EdgeSrc& s, uint64_t idx, uint
     // same-level ids of p above v: for p = v the run starts at sg.y; for
     // p = u, v is entry (idx - hoff[u]) of u's run above u
     const uint32_t cut = (p == v) ? sg.y : sg.y + (uint32_t)(idx - s.hoff[u]) + 1u;
-    return make_uint4((uint32_t)op, sg.x, cut, dp);
+    // sg.w = L(p)
+    return make_uint4((uint32_t)op, sg.w == 1u ? kRootBonus : sg.x, cut, dp);
   } else {
     const int64_t b = (p == u) ? (int64_t)idx + 1 : s.ustart[v];  // neighbours of p above v
     return make_uint4((uint32_t)b, 0u, 0u, (uint32_t)(s.off[p + 1] - b));
   }
 }
 
-__device__ __forceinline__ uint32_t desc_work(uint4 d) { return d.y + (d.w - d.z); }
+__device__ __forceinline__ uint32_t desc_work(uint4 d) {
+  return (d.y & ~kRootBonus) + (d.w - d.z);
+}
 
 // Split point of R2 (relative to base): start of level l+1 for cover.
 template <int M>
@@ -663,6 +674,8 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           const unsigned long long tn = grab();
           const uint4 dn = tn < tb ? descs[tn] : make_uint4(0u, 0u, 0u, 0u);
           const uint32_t* P = pcols + ds.x;
+          const bool bonus = (ds.y & kRootBonus) != 0u;
+          ds.y &= ~kRootBonus;
           unsigned c;
           if (whole) {
             if constexpr (VERT) c = probe_all(P, ds, tab, kHalf, ApexSink{tv});
@@ -685,6 +698,10 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
               probes += m0 + m1 + m2;
               if (we < d) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
             }
+          }
+          if (bonus && wb == 0 && lane == 0) {
+            c += 1u;  // the shared root, on level 0
+            if constexpr (VERT) atomicAdd(&tv[P[0]], 1ull);
           }
           acc += c;
           if (per_edge) {

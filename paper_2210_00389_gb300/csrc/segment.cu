@@ -11,6 +11,7 @@
 //   scols[off[x]+seg.y ..      off[x]+seg.z)   same level, id > x
 //   scols[off[x]+seg.z ..      off[x+1])       neighbours on level L(x)+1
 //
+// and seg.w = L(x).
 // The paper's cost analysis (Sec. III) budgets O(m) for rewriting the
 // neighbour sets after the BFS; this is that step here.  It makes the
 // count-once rule of Alg. 1 / Thm. 2 a property of which segments are
@@ -105,7 +106,7 @@ k_segment_rows(const int64_t* __restrict__ off, const uint32_t* __restrict__ col
         else if (cls[k] == 2) scols[p2++] = w[k];
         else if (cls[k] == 3) scols[p3++] = w[k];
       }
-      seg[xl] = make_uint4(c0, c0 + c1, c0 + c1 + c2, 0u);
+      seg[xl] = make_uint4(c0, c0 + c1, c0 + c1 + c2, lx);
     }
     // rows for the whole warp (long rows are chunked: k_segment_chunks)
     unsigned rows = __ballot_sync(0xFFFFFFFFu, xl < (int64_t)n && dl > kTinyRow && dl <= kLongRow);
@@ -171,7 +172,7 @@ k_segment_rows(const int64_t* __restrict__ off, const uint32_t* __restrict__ col
           p3 += __popc(m[k][3]);
         }
       }
-      if (lane == 0) seg[x] = make_uint4(c0, c0 + c1, c0 + c1 + c2, 0u);
+      if (lane == 0) seg[x] = make_uint4(c0, c0 + c1, c0 + c1 + c2, lx);
     }
   }
 }
@@ -338,7 +339,7 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  : ch.y * (unsigned)kChunk - s_base[0][0] - s_base[0][1] - s_base[0][2];
       scols[b + start + before + s_cnt[cl][k * kChunkWarps + wid] + rank[k]] = w[k];
     }
-    if (ch.y == 0 && threadIdx.x == 0) seg[x] = make_uint4(R0, R0 + R1, R0 + R1 + R2, 0u);
+    if (ch.y == 0 && threadIdx.x == 0) seg[x] = make_uint4(R0, R0 + R1, R0 + R1 + R2, lx);
     __syncthreads();
   }
 }

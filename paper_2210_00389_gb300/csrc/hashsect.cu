@@ -28,7 +28,7 @@
 // <= kSmallOwner keep the warp merge of intersect.cu.  Every other owner is
 // split into work items (owner, slot) of about item_work lookups; a CTA
 // takes an item, builds a two-choice (cuckoo) hash table of N(o) in shared
-// memory (the CTA's whole table, at most 1/3 full; two independent 4-byte
+// memory (the CTA's whole table, at most 2/5 full; two independent 4-byte
 // shared loads per lookup) and its warps take the item's edges from a
 // shared counter.
 // Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (five
@@ -349,7 +349,7 @@ __device__ __forceinline__ uint32_t slot2(uint32_t w, uint32_t nh) {
 // number of threads at once: every key is always in the table or held by
 // exactly one thread).  A chain longer than kMaxKicks gives up and returns
 // false: the key it holds is lost, and the caller rebuilds the table with a
-// smaller window.  At the loads used here (at most 1/3 of the slots) that
+// smaller window.  At the loads used here (at most 2/5 of the slots) that
 // is very rare; a window of one key always fits.
 constexpr int kMaxKicks = 64;
 
@@ -508,25 +508,50 @@ __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, ui
   return probe_ranges(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nh, sink);
 }
 
-// Number of elements <= hi in the sorted run P[a, b), by a 32-ary search
-// with warp ballots: one load per lane per round (a run of at most 32
-// elements takes one round, of at most 1,024 two).
-__device__ __forceinline__ uint32_t count_le(const uint32_t* __restrict__ P, uint32_t a,
-                                             uint32_t b, uint32_t hi) {
+// This window's part of the sorted run P[a, b) -- its elements <= hi, from
+// a on -- looked up with the window bound checked on the loads the lookups
+// use.  A group of kGroup elements whose last element is inside the run
+// and <= hi is wholly in the window (the run is sorted) and is looked up
+// without masks; the first group that is not ends the pass, its elements
+// above hi (or past b) masked out, and the set mask bits (a prefix) are
+// the elements it took.  *m = the number of elements looked up.
+template <class Sink = NoSink>
+__device__ __forceinline__ unsigned probe_window_run(const uint32_t* __restrict__ P, uint32_t a,
+                                                     uint32_t b, uint32_t hi,
+                                                     const uint32_t* tab, uint32_t nh,
+                                                     uint32_t& m, Sink sink = Sink()) {
   const int lane = threadIdx.x & 31;
-  uint32_t lo = a, n = b - a;
-  while (n > 32) {
-    const uint32_t step = (n + 31) / 32;
-    // lane i samples the last element of block i (clamped to the run)
-    const uint32_t e = min(n, (uint32_t)(lane + 1) * step);
-    const unsigned below = __ballot_sync(0xFFFFFFFFu, __ldg(P + lo + e - 1) <= hi);
-    const uint32_t k = (uint32_t)__popc(below);  // blocks wholly <= hi (a prefix: sorted)
-    if (k == 32) return lo + n - a;
-    lo += k * step;  // the boundary lies in block k
-    n = min(step, n - k * step);
+  unsigned c = 0;
+  uint32_t k = a;
+  bool all[kUnroll];
+#pragma unroll
+  for (int j = 0; j < kUnroll; ++j) all[j] = true;
+  while (k < b) {
+    uint32_t w[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) {
+      const uint32_t i = k + j * 32 + lane;
+      w[j] = i < b ? __ldg(P + i) : kEmpty;  // kEmpty > hi
+    }
+    const uint32_t last = __shfl_sync(0xFFFFFFFFu, w[kUnroll - 1], 31);
+    if (last <= hi) {  // the whole group: inside the run and the window
+      c += table_find_n<kUnroll>(tab, nh, w, all, sink);
+      k += kGroup;
+      continue;
+    }
+    bool ok[kUnroll];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) {
+      ok[j] = w[j] <= hi;
+      cnt += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, ok[j]));
+    }
+    c += table_find_n<kUnroll>(tab, nh, w, ok, sink);
+    k += cnt;
+    break;
   }
-  const bool in = (uint32_t)lane < n && __ldg(P + lo + lane) <= hi;
-  return lo - a + (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, in));
+  m = k - a;
+  return c;
 }
 
 constexpr uint32_t kBatchMaxWork = 64;  // tasks with fewer lookups share a warp pass
@@ -686,14 +711,16 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
             const uint32_t z = task_split[t];
             uint4 cur = wb == 0 ? make_uint4(0u, ds.z, z, 0u) : cursors[t];
             // this window's elements of each run: the prefix <= hi
-            const uint32_t m0 = count_le(P, cur.x, ds.y, hi);
-            const uint32_t m1 = count_le(P, cur.y, z, hi);
-            const uint32_t m2 = count_le(P, cur.z, ds.w, hi);
-            if constexpr (VERT)
-              c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf,
-                               ApexSink{tv});
-            else
-              c = probe_ranges(P + cur.x, m0, P + cur.y, m1, P + cur.z, m2, tab, kHalf);
+            uint32_t m0, m1, m2;
+            if constexpr (VERT) {
+              c = probe_window_run(P, cur.x, ds.y, hi, tab, kHalf, m0, ApexSink{tv});
+              c += probe_window_run(P, cur.y, z, hi, tab, kHalf, m1, ApexSink{tv});
+              c += probe_window_run(P, cur.z, ds.w, hi, tab, kHalf, m2, ApexSink{tv});
+            } else {
+              c = probe_window_run(P, cur.x, ds.y, hi, tab, kHalf, m0);
+              c += probe_window_run(P, cur.y, z, hi, tab, kHalf, m1);
+              c += probe_window_run(P, cur.z, ds.w, hi, tab, kHalf, m2);
+            }
             if (lane == 0) {
               probes += m0 + m1 + m2;
               if (we < d) cursors[t] = make_uint4(cur.x + m0, cur.y + m1, cur.z + m2, 0u);
@@ -749,19 +776,19 @@ constexpr int kMedThreads = 256, kMedSlots = 8192, kMedPerSM = 5;
 constexpr int kBigThreads = 1024, kBigSlots = 57344, kBigPerSM = 1;
 // Owner entries per table window, per mode (cover, plain): every owner row
 // longer than this is processed in windows, and each window pass revisits
-// all the owner's edges.  The two-choice table stays at most 1/3 full
-// (windows of 19,104 measured faster than 14,336 for cover on R-MAT scale
-// 22 and Chung-Lu 2^23).
+// all the owner's edges.  The two-choice table stays at most 2/5 full
+// (windows of 22,936 measured faster than 19,104 and 14,336 on R-MAT scale
+// 22 and 26 and Chung-Lu 2^23).
 constexpr int kMedWin = (int)kMediumMax;
 // Medium owners' edges with fewer than kBatchMaxWork lookups share warp
 // passes (probe_batch) in plain mode, whose upper-neighbour probe lists are
 // often that short; cover probe lists rarely are.  Measured on R-MAT scale
 // 20 and 22.
 constexpr bool kMedBatch[2] = {false, true};
-constexpr int kBigWin[2] = {19104, 19104};
-static_assert(3 * kMedWin <= kMedSlots && 3 * kBigWin[0] <= kBigSlots &&
-                  3 * kBigWin[1] <= kBigSlots,
-              "two-choice tables at most 1/3 full");
+constexpr int kBigWin[2] = {22936, 22936};
+static_assert(3 * kMedWin <= kMedSlots && 5 * kBigWin[0] <= 2 * kBigSlots &&
+                  5 * kBigWin[1] <= 2 * kBigSlots,
+              "two-choice tables at most 2/5 full");
 static_assert(kMedSlots % 8 == 0 && kBigSlots % 8 == 0, "tables in whole 16-byte halves");
 
 template <int M, int THREADS, int SLOTS, int WIN, int MINB, bool BATCH, bool VERT = false>

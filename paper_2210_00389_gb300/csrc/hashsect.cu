@@ -116,11 +116,12 @@ __device__ __forceinline__ void owner_probe(const int64_t* off, uint32_t u, uint
 // plain).
 template <int M>
 __device__ __forceinline__ uint4 probe_desc(const EdgeSrc& s, uint64_t idx, uint32_t u, uint32_t v,
-                                            uint32_t p) {
+                                            uint32_t p, uint32_t* split = nullptr) {
   if (M == kModeCover) {
     const int64_t op = s.off[p];
     const uint32_t dp = (uint32_t)(s.off[p + 1] - op);
     const uint4 sg = s.seg[p];
+    if (split) *split = sg.z;  // start of level l+1: where R2's two sorted pieces meet
     // same-level ids of p above v: for p = v the run starts at sg.y; for
     // p = u, v is entry (idx - hoff[u]) of u's run above u
     const uint32_t cut = (p == v) ? sg.y : sg.y + (uint32_t)(idx - s.hoff[u]) + 1u;
@@ -128,19 +129,14 @@ __device__ __forceinline__ uint4 probe_desc(const EdgeSrc& s, uint64_t idx, uint
     return make_uint4((uint32_t)op, sg.w == 1u ? kRootBonus : sg.x, cut, dp);
   } else {
     const int64_t b = (p == u) ? (int64_t)idx + 1 : s.ustart[v];  // neighbours of p above v
-    return make_uint4((uint32_t)b, 0u, 0u, (uint32_t)(s.off[p + 1] - b));
+    const uint4 d = make_uint4((uint32_t)b, 0u, 0u, (uint32_t)(s.off[p + 1] - b));
+    if (split) *split = d.w;
+    return d;
   }
 }
 
 __device__ __forceinline__ uint32_t desc_work(uint4 d) {
   return (d.y & ~kRootBonus) + (d.w - d.z);
-}
-
-// Split point of R2 (relative to base): start of level l+1 for cover.
-template <int M>
-__device__ __forceinline__ uint32_t probe_split(const EdgeSrc& s, uint32_t p, uint4 d) {
-  if (M == kModeCover) return s.seg[p].z;
-  return d.w;
 }
 
 // ------------------------------------------------------------------ bucketing
@@ -214,13 +210,18 @@ __device__ __forceinline__ bool owner_hashed(unsigned long long work, uint32_t d
 
 // Scatter every hashed edge's descriptor (and its index, for per-edge
 // counts) into its owner's task range; edges of owners too light to hash
-// are appended to the merge list.
+// are appended to the merge list.  ostart[o] is the owner's cursor: its
+// first task index, advanced here by one per edge (so it ends at the
+// owner's last task + 1), with bit kLightBit set by k_item_counts for
+// owners too light to hash -- one atomic per owner and warp both places an
+// edge and tells whether it is hashed, with no other per-owner read.
+constexpr unsigned long long kLightBit = 1ull << 63;
+
 template <int M>
-__global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long long* __restrict__ ostart,
-                                 const unsigned long long* __restrict__ owner_work,
-                                 uint32_t* __restrict__ cursor, uint4* __restrict__ descs,
-                                 uint32_t* __restrict__ task_split, uint32_t* __restrict__ task_idx,
-                                 uint32_t* __restrict__ small_list, unsigned long long* ctrl) {
+__global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, unsigned long long* __restrict__ ostart,
+                                 uint4* __restrict__ descs, uint32_t* __restrict__ task_split,
+                                 uint32_t* __restrict__ task_idx, uint32_t* __restrict__ small_list,
+                                 unsigned long long* ctrl) {
   const int lane = threadIdx.x & 31;
   uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -231,23 +232,25 @@ __global__ void k_bucket_scatter(EdgeSrc s, uint64_t nidx, const unsigned long l
     if (idx < nidx && edge_at<M>(s, gi, u, v)) {
       uint32_t dout;
       owner_probe(s.off, u, v, o, p, dout);
-      if (dout > kSmallOwner) {
-        if (owner_hashed(owner_work[o], dout)) key = o;
-        else light = true;
-      }
+      if (dout > kSmallOwner) key = o;
     }
-    // one cursor atomic per owner among the warp's lanes
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
     if (key != kEmpty) {
+      // the descriptor's loads go out before the cursor atomic returns
+      uint32_t z;
+      const uint4 d = probe_desc<M>(s, gi, u, v, p, &z);
       const int leader = __ffs(peers) - 1;
-      uint32_t c0 = 0;
-      if (lane == leader) c0 = atomicAdd(&cursor[key], (uint32_t)__popc(peers));
+      unsigned long long c0 = 0;
+      if (lane == leader) c0 = atomicAdd(&ostart[key], (unsigned long long)__popc(peers));
       c0 = __shfl_sync(peers, c0, leader);
-      const unsigned long long t = ostart[key] + c0 + __popc(peers & ((1u << lane) - 1u));
-      const uint4 d = probe_desc<M>(s, gi, u, v, p);
-      descs[t] = d;
-      task_split[t] = probe_split<M>(s, p, d);
-      if (task_idx) task_idx[t] = (uint32_t)gi;
+      if (c0 & kLightBit) {
+        light = true;
+      } else {
+        const unsigned long long t = c0 + __popc(peers & ((1u << lane) - 1u));
+        descs[t] = d;
+        task_split[t] = z;
+        if (task_idx) task_idx[t] = (uint32_t)gi;
+      }
     }
     const unsigned m = __ballot_sync(0xFFFFFFFFu, light);
     if (m) {
@@ -279,18 +282,24 @@ __device__ __forceinline__ uint32_t owner_slots(uint32_t cnt, unsigned long long
 __device__ __forceinline__ int owner_class(uint32_t d) { return d > kMediumMax ? 1 : 0; }
 
 // Per owner: its slot count; totals per class in ctrl[kCtrlItems + class].
+// Owners with edges that are too light to hash get kLightBit in ostart.
 __global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
                               const uint32_t* __restrict__ owner_cnt,
                               const unsigned long long* __restrict__ owner_work,
                               unsigned long long item_lo, unsigned long long item_hi,
-                              unsigned long long item_div, unsigned long long* ctrl) {
+                              unsigned long long item_div, unsigned long long* ctrl,
+                              unsigned long long* __restrict__ ostart) {
   const unsigned long long item_work = item_work_of(ctrl, item_lo, item_hi, item_div);
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long t[2] = {0ull, 0ull};
   for (; o < (int64_t)n; o += stride) {
     const uint32_t d = degree(off, (uint32_t)o);
-    t[owner_class(d)] += owner_slots(owner_cnt[o], owner_work[o], d, item_work);
+    const uint32_t cnt = owner_cnt[o];
+    if (cnt == 0) continue;
+    const unsigned long long w = owner_work[o];
+    if (!owner_hashed(w, d)) ostart[o] |= kLightBit;
+    t[owner_class(d)] += owner_slots(cnt, w, d, item_work);
   }
   for (int c = 0; c < 2; ++c) {
     unsigned long long x = t[c];
@@ -500,6 +509,21 @@ __device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0
   return c;
 }
 
+// Asks L2 to fetch elements [kGroup, len) of the run R (at most kPrefetchMax
+// bytes): one bulk prefetch, issued by one lane, with no registers held
+// while it is in flight.  The range is shrunk to 16-byte boundaries inside
+// the run, so it never leaves the array.
+constexpr uint32_t kPrefetchMax = 32768;
+__device__ __forceinline__ void prefetch_run_l2(const uint32_t* R, uint32_t len) {
+  if (len <= kGroup + 8u) return;
+  const uintptr_t a = ((uintptr_t)(R + kGroup) + 15u) & ~(uintptr_t)15u;
+  uintptr_t e = (uintptr_t)(R + len) & ~(uintptr_t)15u;
+  if (e > a + kPrefetchMax) e = a + kPrefetchMax;
+  if (e <= a) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a))
+               : "memory");
+}
+
 // All probe elements of a descriptor: runs [0, x) and [cut, end) of P.
 template <class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
@@ -646,7 +670,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
   for (uint64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const uint2 item = items[it];
     const uint32_t o = item.x, slot = item.y >> 16, nsl = item.y & 0xFFFFu;
-    const uint64_t T0 = ostart[o], T = owner_cnt[o];
+    const uint64_t T = owner_cnt[o], T0 = ostart[o] - T;  // ostart: the scatter's end cursor
     const uint64_t ta = T0 + T * slot / nsl, tb = T0 + T * (slot + 1) / nsl;
     const int64_t ro = off[o];
     const uint32_t d = (uint32_t)(off[o + 1] - ro);
@@ -703,6 +727,10 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
           ds.y &= ~kRootBonus;
           unsigned c;
           if (whole) {
+            if (lane == 0) {
+              prefetch_run_l2(P, ds.y);
+              prefetch_run_l2(P + ds.z, ds.w - ds.z);
+            }
             if constexpr (VERT) c = probe_all(P, ds, tab, kHalf, ApexSink{tv});
             else c = probe_all(P, ds, tab, kHalf);
             if (lane == 0) probes += desc_work(ds);
@@ -822,18 +850,16 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
                            const int64_t* ustart, uint32_t* per_edge, unsigned long long* tv) {
   cudaStream_t st = g->stream;
   const int T = 256;
-  DevBuf<uint32_t> owner_cnt, cursor, small_list, task_idx, task_split;
+  DevBuf<uint32_t> owner_cnt, small_list, task_idx, task_split;
   DevBuf<unsigned long long> owner_work, ostart, counters;
   DevBuf<uint4> descs, cursors;
   DevBuf<uint2> items0, items1;
   TC_TRY(owner_cnt.alloc(g->n, st));
-  TC_TRY(cursor.alloc(g->n, st));
   TC_TRY(owner_work.alloc(g->n, st));
   TC_TRY(ostart.alloc(g->n, st));
   TC_TRY(small_list.alloc(nidx, st));
   TC_TRY(counters.alloc(4, st));
   TC_CUDA(cudaMemsetAsync(owner_cnt.p, 0, sizeof(uint32_t) * g->n, st));
-  TC_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(uint32_t) * g->n, st));
   TC_CUDA(cudaMemsetAsync(owner_work.p, 0, sizeof(unsigned long long) * g->n, st));
   TC_CUDA(cudaMemsetAsync(counters.p, 0, 4 * sizeof(unsigned long long), st));
   TC_CUDA(cudaMemsetAsync(g->ctrl.p + kCtrlQ0, 0, sizeof(unsigned long long), st));
@@ -845,7 +871,7 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   launch(k_u32_to_u64, grid_for(g->n, T), T, 0, st, owner_cnt.p, g->n, ostart.p);
   TC_TRY(exclusive_scan_u64(ostart.p, g->n, g->ctrl.p + kCtrlTmp, st));
   launch(k_item_counts, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-         kItemMin[M], kItemMax[M], item_div, g->ctrl.p);
+         kItemMin[M], kItemMax[M], item_div, g->ctrl.p, ostart.p);
   TC_CUDA(cudaGetLastError());
   TC_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl.p, kCtrlSlots * sizeof(unsigned long long),
                           cudaMemcpyDeviceToHost, st));
@@ -862,8 +888,8 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
   TC_TRY(items1.alloc(nitems1, st));
   if (ntasks > 0) {
     launch(k_bucket_scatter<M>, grid_for((int64_t)nidx, T, 16), T, 0, st, s, nidx, ostart.p,
-           owner_work.p, cursor.p, descs.p, task_split.p,
-           need_idx ? task_idx.p : (uint32_t*)nullptr, small_list.p, g->ctrl.p);
+           descs.p, task_split.p, need_idx ? task_idx.p : (uint32_t*)nullptr, small_list.p,
+           g->ctrl.p);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
            kItemMin[M], kItemMax[M], item_div, g->ctrl.p, items0.p, items1.p, counters.p);
   }

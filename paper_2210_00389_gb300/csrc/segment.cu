@@ -33,8 +33,13 @@ constexpr int kSegThreads = 256;
 
 // Segment of neighbour w (level lw) in the row of x (level lx): 0 = level
 // below, 1 = same level and id < x, 2 = same level and id > x, 3 = above.
+// A neighbour's level differs from x's by at most one (levels are BFS
+// distances), so the levels are needed only modulo 256: lw may come from a
+// byte copy of the levels (LT = uint8_t), which stays resident in L2 where
+// the 32-bit levels of a large graph do not.
 __device__ __forceinline__ int seg_class(uint32_t w, uint32_t lw, uint32_t x, uint32_t lx) {
-  return lw < lx ? 0 : (lw == lx ? (w < x ? 1 : 2) : 3);
+  const uint32_t d = (lw - lx) & 0xFFu;
+  return d == 0u ? (w < x ? 1 : 2) : (d == 1u ? 3 : 0);
 }
 
 constexpr int kTinyRow = 8;  // rows this short are partitioned by one thread
@@ -43,8 +48,9 @@ constexpr int kSegBlock = 32 * kSegUnroll;  // entries a warp loads at once
 
 // Entries [base, base + kSegBlock) of a row ending at e: lane entries
 // base + 32 k + lane with their segment class (-1 past the row).
+template <class LT>
 __device__ __forceinline__ void seg_load_block(const uint32_t* __restrict__ cols,
-                                               const uint32_t* __restrict__ L, int64_t base,
+                                               const LT* __restrict__ B, int64_t base,
                                                int64_t e, uint32_t x, uint32_t lx,
                                                uint32_t (&w)[kSegUnroll], int (&cls)[kSegUnroll]) {
   const int lane = threadIdx.x & 31;
@@ -56,7 +62,7 @@ __device__ __forceinline__ void seg_load_block(const uint32_t* __restrict__ cols
 #pragma unroll
   for (int k = 0; k < kSegUnroll; ++k) {
     const int64_t i = base + 32 * k + lane;
-    cls[k] = i < e ? seg_class(w[k], L[w[k]], x, lx) : -1;
+    cls[k] = i < e ? seg_class(w[k], B[w[k]], x, lx) : -1;
   }
 }
 
@@ -65,11 +71,13 @@ __device__ __forceinline__ void seg_load_block(const uint32_t* __restrict__ cols
 // loads issued at once); the longer rows are then taken one at a time by
 // the whole warp, in blocks of kSegBlock entries classified and ranked
 // inside their segment by warp ballots.  A row of one block takes one pass;
-// a longer one counts its segments first.
+// a longer one counts its segments first.  L: levels; B: the levels read for
+// neighbours (L itself, or its byte copy).
+template <class LT>
 __global__ void __launch_bounds__(kSegThreads)
 k_segment_rows(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
-               const uint32_t* __restrict__ L, uint32_t n, uint32_t* __restrict__ scols,
-               uint4* __restrict__ seg) {
+               const uint32_t* __restrict__ L, const LT* __restrict__ B, uint32_t n,
+               uint32_t* __restrict__ scols, uint4* __restrict__ seg) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
@@ -90,7 +98,7 @@ k_segment_rows(const int64_t* __restrict__ off, const uint32_t* __restrict__ col
       for (int k = 0; k < kTinyRow; ++k) w[k] = k < dl ? cols[bl + k] : 0u;
 #pragma unroll
       for (int k = 0; k < kTinyRow; ++k)
-        cls[k] = k < dl ? seg_class(w[k], L[w[k]], (uint32_t)xl, lx) : -1;
+        cls[k] = k < dl ? seg_class(w[k], B[w[k]], (uint32_t)xl, lx) : -1;
       unsigned c0 = 0, c1 = 0, c2 = 0;
 #pragma unroll
       for (int k = 0; k < kTinyRow; ++k) {
@@ -123,7 +131,7 @@ k_segment_rows(const int64_t* __restrict__ off, const uint32_t* __restrict__ col
         for (int64_t base = b; base < e; base += kSegBlock) {
           uint32_t w[kSegUnroll];
           int cls[kSegUnroll];
-          seg_load_block(cols, L, base, e, (uint32_t)x, lx, w, cls);
+          seg_load_block(cols, B, base, e, (uint32_t)x, lx, w, cls);
 #pragma unroll
           for (int k = 0; k < kSegUnroll; ++k) {
             c0 += cls[k] == 0;
@@ -142,34 +150,34 @@ k_segment_rows(const int64_t* __restrict__ off, const uint32_t* __restrict__ col
       for (int64_t base = b; base < e; base += kSegBlock) {
         uint32_t w[kSegUnroll];
         int cls[kSegUnroll];
-        seg_load_block(cols, L, base, e, (uint32_t)x, lx, w, cls);
-        unsigned m[kSegUnroll][4];
-#pragma unroll
-        for (int k = 0; k < kSegUnroll; ++k)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) m[k][j] = __ballot_sync(0xFFFFFFFFu, cls[k] == j);
+        seg_load_block(cols, B, base, e, (uint32_t)x, lx, w, cls);
         if (e - b <= kSegBlock) {
           // one block: the segment sizes are its ballot counts
 #pragma unroll
           for (int k = 0; k < kSegUnroll; ++k) {
-            c0 += __popc(m[k][0]);
-            c1 += __popc(m[k][1]);
-            c2 += __popc(m[k][2]);
+            c0 += __popc(__ballot_sync(0xFFFFFFFFu, cls[k] == 0));
+            c1 += __popc(__ballot_sync(0xFFFFFFFFu, cls[k] == 1));
+            c2 += __popc(__ballot_sync(0xFFFFFFFFu, cls[k] == 2));
           }
           p1 = b + c0;
           p2 = b + c0 + c1;
           p3 = b + c0 + c1 + c2;
         }
+        // ballots taken per round and used at once (few masks live)
 #pragma unroll
         for (int k = 0; k < kSegUnroll; ++k) {
-          if (cls[k] == 0) scols[p0 + __popc(m[k][0] & lt)] = w[k];
-          else if (cls[k] == 1) scols[p1 + __popc(m[k][1] & lt)] = w[k];
-          else if (cls[k] == 2) scols[p2 + __popc(m[k][2] & lt)] = w[k];
-          else if (cls[k] == 3) scols[p3 + __popc(m[k][3] & lt)] = w[k];
-          p0 += __popc(m[k][0]);
-          p1 += __popc(m[k][1]);
-          p2 += __popc(m[k][2]);
-          p3 += __popc(m[k][3]);
+          const unsigned m0 = __ballot_sync(0xFFFFFFFFu, cls[k] == 0);
+          const unsigned m1 = __ballot_sync(0xFFFFFFFFu, cls[k] == 1);
+          const unsigned m2 = __ballot_sync(0xFFFFFFFFu, cls[k] == 2);
+          const unsigned m3 = __ballot_sync(0xFFFFFFFFu, cls[k] == 3);
+          if (cls[k] == 0) scols[p0 + __popc(m0 & lt)] = w[k];
+          else if (cls[k] == 1) scols[p1 + __popc(m1 & lt)] = w[k];
+          else if (cls[k] == 2) scols[p2 + __popc(m2 & lt)] = w[k];
+          else if (cls[k] == 3) scols[p3 + __popc(m3 & lt)] = w[k];
+          p0 += __popc(m0);
+          p1 += __popc(m1);
+          p2 += __popc(m2);
+          p3 += __popc(m3);
         }
       }
       if (lane == 0) seg[x] = make_uint4(c0, c0 + c1, c0 + c1 + c2, lx);
@@ -186,10 +194,11 @@ constexpr int kChunkWarps = kChunkThreads / 32;
 static_assert(kChunkPer * kChunkWarps == 32, "one warp scans a chunk's (sub-chunk, warp) counts");
 
 // Long rows, pass 1: the chunk's segment sizes.
+template <class LT>
 __global__ void __launch_bounds__(kChunkThreads)
 k_segment_chunk_counts(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
-                       const uint32_t* __restrict__ L, const uint2* __restrict__ lchunks,
-                       int64_t nch, uint4* __restrict__ ccnt) {
+                       const uint32_t* __restrict__ L, const LT* __restrict__ B,
+                       const uint2* __restrict__ lchunks, int64_t nch, uint4* __restrict__ ccnt) {
   __shared__ unsigned red[3][kChunkWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
@@ -207,7 +216,7 @@ k_segment_chunk_counts(const int64_t* __restrict__ off, const uint32_t* __restri
 #pragma unroll
     for (int k = 0; k < kChunkPer; ++k) {
       if (w[k] != kUnvisited) {
-        const int cls = seg_class(w[k], L[w[k]], x, lx);
+        const int cls = seg_class(w[k], B[w[k]], x, lx);
         a0 += cls == 0;
         a1 += cls == 1;
         a2 += cls == 2;
@@ -242,11 +251,12 @@ k_segment_chunk_counts(const int64_t* __restrict__ off, const uint32_t* __restri
 // contiguous in lchunks); then a stable scatter of the chunk, ranked by
 // __match_any_sync inside a warp and a scan over the chunk's (sub-chunk,
 // warp) counts.  The row's first chunk writes seg.
+template <class LT>
 __global__ void __launch_bounds__(kChunkThreads)
 k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
-                 const uint32_t* __restrict__ L, const uint2* __restrict__ lchunks, int64_t nch,
-                 const uint4* __restrict__ ccnt, uint32_t* __restrict__ scols,
-                 uint4* __restrict__ seg) {
+                 const uint32_t* __restrict__ L, const LT* __restrict__ B,
+                 const uint2* __restrict__ lchunks, int64_t nch, const uint4* __restrict__ ccnt,
+                 uint32_t* __restrict__ scols, uint4* __restrict__ seg) {
   __shared__ unsigned s_tot[2][3][kChunkWarps];  // [before this chunk / whole row][segment][warp]
   __shared__ unsigned s_cnt[4][32];  // [segment][sub-chunk * warps + warp]: then exclusive scan
   __shared__ unsigned s_base[2][3];
@@ -284,7 +294,7 @@ k_segment_chunks(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
       }
 #pragma unroll
     for (int k = 0; k < kChunkPer; ++k)
-      cls[k] = w[k] != kUnvisited ? seg_class(w[k], L[w[k]], x, lx) : -1;
+      cls[k] = w[k] != kUnvisited ? seg_class(w[k], B[w[k]], x, lx) : -1;
     unsigned rank[kChunkPer];
 #pragma unroll
     for (int k = 0; k < kChunkPer; ++k) {
@@ -420,23 +430,46 @@ k_cover_gather_chunks(const int64_t* __restrict__ off, const uint32_t* __restric
   }
 }
 
+__global__ void k_levels_u8(const uint32_t* __restrict__ L, uint32_t n, uint8_t* __restrict__ B) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < (int64_t)n; i += stride) B[i] = (uint8_t)L[i];
+}
+
+// Graphs with more vertices than this read neighbour levels from a byte copy
+// (n bytes instead of 4n: at R-MAT scale 26 67 MB, which L2 holds).
+constexpr uint32_t kByteLevelsMin = 1u << 23;
+
+template <class LT>
+static void launch_segments(tc_graph* g, const LT* B, uint4* ccnt) {
+  cudaStream_t s = g->stream;
+  if (g->n > 0)
+    launch(k_segment_rows<LT>, grid_for((int64_t)g->n * 32, kSegThreads, 16), kSegThreads, 0, s,
+           g->off, g->cols, g->levels.p, B, g->n, g->scols.p, g->seg.p);
+  if (g->nlchunks > 0) {
+    const int grid = (int)std::min<int64_t>(g->nlchunks, (int64_t)sm_count() * 8);
+    launch(k_segment_chunk_counts<LT>, grid, kChunkThreads, 0, s, g->off, g->cols, g->levels.p, B,
+           g->lchunks.p, g->nlchunks, ccnt);
+    launch(k_segment_chunks<LT>, grid, kChunkThreads, 0, s, g->off, g->cols, g->levels.p, B,
+           g->lchunks.p, g->nlchunks, ccnt, g->scols.p, g->seg.p);
+  }
+}
+
 int compute_segments(tc_graph* g) {
   cudaStream_t s = g->stream;
   if (g->nlevels < 0) TC_TRY(compute_levels(g, nullptr, 0));
   if (g->seg_valid) return TC_OK;
   TC_TRY(g->scols.reserve((size_t)g->nnz, s));
   TC_TRY(g->seg.reserve(g->n, s));
-  if (g->n > 0)
-    launch(k_segment_rows, grid_for((int64_t)g->n * 32, kSegThreads, 16), kSegThreads, 0, s,
-           g->off, g->cols, g->levels.p, g->n, g->scols.p, g->seg.p);
-  if (g->nlchunks > 0) {
-    DevBuf<uint4> ccnt;
-    TC_TRY(ccnt.alloc((size_t)g->nlchunks, s));
-    const int grid = (int)std::min<int64_t>(g->nlchunks, (int64_t)sm_count() * 8);
-    launch(k_segment_chunk_counts, grid, kChunkThreads, 0, s, g->off, g->cols, g->levels.p,
-           g->lchunks.p, g->nlchunks, ccnt.p);
-    launch(k_segment_chunks, grid, kChunkThreads, 0, s, g->off, g->cols, g->levels.p,
-           g->lchunks.p, g->nlchunks, ccnt.p, g->scols.p, g->seg.p);
+  DevBuf<uint4> ccnt;
+  if (g->nlchunks > 0) TC_TRY(ccnt.alloc((size_t)g->nlchunks, s));
+  if (g->n > kByteLevelsMin) {
+    DevBuf<uint8_t> b;
+    TC_TRY(b.alloc(g->n, s));
+    launch(k_levels_u8, grid_for(g->n, kSegThreads), kSegThreads, 0, s, g->levels.p, g->n, b.p);
+    launch_segments<uint8_t>(g, b.p, ccnt.p);
+  } else {
+    launch_segments<uint32_t>(g, g->levels.p, ccnt.p);
   }
   TC_CUDA(cudaGetLastError());
   g->seg_valid = true;

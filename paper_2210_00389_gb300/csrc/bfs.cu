@@ -420,6 +420,7 @@ int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots) {
   TC_TRY(droots.alloc(rl.size(), s));
   TC_CUDA(cudaMemcpyAsync(droots.p, rl.data(), rl.size() * sizeof(uint32_t),
                           cudaMemcpyHostToDevice, s));
+  TC_TRY(ensure_erow(g));
   launch(k_cc_init, grid_for(n, T), T, 0, s, g->off, g->cols, n, P.p);
   if (g->nnz > 0) launch(k_cc_hook, grid_for(g->nnz, T), T, 0, s, g->erow.p, g->cols, g->nnz, P.p);
   launch(k_cc_flatten, grid_for(n, T), T, 0, s, n, P.p);

@@ -1,8 +1,10 @@
-// Graph ingest (a0): copy the caller's CSR to the device, check it, build
-// the COO row index of every entry, find the maximum-degree vertex.
+// Graph ingest (a0): copy the caller's CSR to the device, check it, list the
+// chunks of its long rows, find the maximum-degree vertex; the COO row index
+// of every entry is built when a path first needs it.
 //
 // Input format: a symmetric compressed-sparse-row graph, the input format of
 // Sec. III of Bader et al., "Triangle Counting Through Cover-Edges".
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -65,45 +67,72 @@ __global__ void k_check_offsets(const int64_t* __restrict__ off, uint32_t n, int
   }
 }
 
-// Warp per vertex: write erow[e] = u for the row, check column range, and,
-// when `strict`, no self-loops and strictly ascending rows.  A row longer
-// than kLongRow is not walked here: the warp lists its chunks (lchunks) and
-// k_rows_long does them, one CTA per chunk.
+// Rows with at most this many entries are checked (and given their COO row
+// ids) by one lane.
+constexpr int kTinyRowG = 8;
+
+// A warp takes 32 consecutive rows: a lane checks its own row if it has at
+// most kTinyRowG entries (all its loads issued at once), the rows up to
+// kLongRow entries are then checked by the whole warp one at a time, and a
+// row longer than kLongRow is listed as chunks (lchunks, each row's chunks
+// contiguous) for k_rows_long.  Checks: column range always; when `strict`,
+// no self-loops and strictly ascending rows.
 __global__ void k_rows_and_check(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols,
-                                 uint32_t n, uint32_t* __restrict__ erow, int strict,
-                                 uint2* __restrict__ lchunks, unsigned long long* ctrl) {
+                                 uint32_t n, int strict, uint2* __restrict__ lchunks,
+                                 unsigned long long* ctrl) {
   const int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long err = 0;
-  for (int64_t u = warp; u < (int64_t)n; u += nwarps) {
-    int64_t b = off[u], e = off[u + 1];
-    if (e - b > kLongRow) {
-      const uint32_t nch = (uint32_t)((e - b + kChunk - 1) / kChunk);
-      unsigned long long c0 = 0;
-      if (lane == 0) c0 = atomicAdd(&ctrl[kCtrlLong], (unsigned long long)nch);
-      c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
-      for (uint32_t k = lane; k < nch; k += 32) lchunks[c0 + k] = make_uint2((uint32_t)u, k);
-      continue;
+  for (int64_t gbase = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; gbase < (int64_t)n;
+       gbase += gstride) {
+    const int64_t x = gbase + lane;
+    int64_t b = 0, e = 0;
+    if (x < (int64_t)n) {
+      b = off[x];
+      e = off[x + 1];
     }
-    for (int64_t i = b + lane; i < e; i += 32) {
-      uint32_t v = cols[i];
-      erow[i] = (uint32_t)u;
-      if (v >= n) err |= kErrColRange;
-      if (strict) {
-        if (v == (uint32_t)u) err |= kErrSelfLoop;
-        if (i > b && cols[i - 1] >= v) err |= kErrUnsorted;
+    const int64_t d = e - b;
+    if (x < (int64_t)n && d <= kTinyRowG) {
+      uint32_t w[kTinyRowG];
+#pragma unroll
+      for (int k = 0; k < kTinyRowG; ++k) w[k] = k < d ? cols[b + k] : 0u;
+#pragma unroll
+      for (int k = 0; k < kTinyRowG; ++k) {
+        if (k >= d) break;
+        if (w[k] >= n) err |= kErrColRange;
+        if (strict) {
+          if (w[k] == (uint32_t)x) err |= kErrSelfLoop;
+          if (k > 0 && w[k - 1] >= w[k]) err |= kErrUnsorted;
+        }
+      }
+    } else if (x < (int64_t)n && d > kLongRow) {
+      const uint32_t nch = (uint32_t)((d + kChunk - 1) / kChunk);
+      const unsigned long long c0 = atomicAdd(&ctrl[kCtrlLong], (unsigned long long)nch);
+      for (uint32_t k = 0; k < nch; ++k) lchunks[c0 + k] = make_uint2((uint32_t)x, k);
+    }
+    unsigned rows = __ballot_sync(0xFFFFFFFFu, x < (int64_t)n && d > kTinyRowG && d <= kLongRow);
+    while (rows) {
+      const int r = __ffs(rows) - 1;
+      rows &= rows - 1;
+      const uint32_t u = (uint32_t)(gbase + r);
+      const int64_t rb = __shfl_sync(0xFFFFFFFFu, b, r), re = __shfl_sync(0xFFFFFFFFu, e, r);
+      for (int64_t i = rb + lane; i < re; i += 32) {
+        const uint32_t v = cols[i];
+        if (v >= n) err |= kErrColRange;
+        if (strict) {
+          if (v == u) err |= kErrSelfLoop;
+          if (i > rb && cols[i - 1] >= v) err |= kErrUnsorted;
+        }
       }
     }
   }
   if (err) atomicOr(&ctrl[kCtrlErr], err);
 }
 
-// CTA per chunk of a long row: the same work as k_rows_and_check.
+// CTA per chunk of a long row: the same checks as k_rows_and_check.
 __global__ void __launch_bounds__(kChunk)
 k_rows_long(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
-            uint32_t* __restrict__ erow, int strict, const uint2* __restrict__ lchunks,
-            unsigned long long* ctrl) {
+            int strict, const uint2* __restrict__ lchunks, unsigned long long* ctrl) {
   const unsigned long long nch = ctrl[kCtrlLong];
   unsigned long long err = 0;
   for (unsigned long long c = blockIdx.x; c < nch; c += gridDim.x) {
@@ -113,7 +142,6 @@ k_rows_long(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols, 
     const int64_t i = b + (int64_t)ch.y * kChunk + threadIdx.x;
     if (i < e) {
       const uint32_t v = cols[i];
-      erow[i] = u;
       if (v >= n) err |= kErrColRange;
       if (strict) {
         if (v == u) err |= kErrSelfLoop;
@@ -122,6 +150,43 @@ k_rows_long(const int64_t* __restrict__ off, const uint32_t* __restrict__ cols, 
     }
   }
   if (err) atomicOr(&ctrl[kCtrlErr], err);
+}
+
+// COO row ids: erow[i] = u for every entry i of row u, in the same row
+// classes (a lane for tiny rows, the warp for rows up to kLongRow, a CTA per
+// chunk of the longer rows).
+__global__ void k_erow_rows(const int64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ erow) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t gbase = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; gbase < (int64_t)n;
+       gbase += gstride) {
+    const int64_t x = gbase + lane;
+    int64_t b = 0, e = 0;
+    if (x < (int64_t)n) {
+      b = off[x];
+      e = off[x + 1];
+    }
+    const int64_t d = e - b;
+    if (x < (int64_t)n && d <= kTinyRowG)
+      for (int64_t i = b; i < e; ++i) erow[i] = (uint32_t)x;
+    unsigned rows = __ballot_sync(0xFFFFFFFFu, x < (int64_t)n && d > kTinyRowG && d <= kLongRow);
+    while (rows) {
+      const int r = __ffs(rows) - 1;
+      rows &= rows - 1;
+      const int64_t rb = __shfl_sync(0xFFFFFFFFu, b, r), re = __shfl_sync(0xFFFFFFFFu, e, r);
+      for (int64_t i = rb + lane; i < re; i += 32) erow[i] = (uint32_t)(gbase + r);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_erow_long(const int64_t* __restrict__ off, const uint2* __restrict__ lchunks, int64_t nch,
+            uint32_t* __restrict__ erow) {
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const uint2 ch = lchunks[c];
+    const int64_t i = off[ch.x] + (int64_t)ch.y * kChunk + threadIdx.x;
+    if (i < off[ch.x + 1]) erow[i] = ch.x;
+  }
 }
 
 // Thread per entry: (u, v) must have (v, u); binary search of u in N(v).
@@ -199,6 +264,21 @@ static int describe_err(tc_graph* g, unsigned long long err) {
   return fail(TC_ERR_INVALID_GRAPH, "graph check failed (0x%llx)", err);
 }
 
+// The COO row ids are built on first use (the plain path, the symmetry
+// check, explicit BFS roots); the cover path with the default roots never
+// reads them.  Needs g->nlchunks.
+int ensure_erow(tc_graph* g) {
+  if (g->erow.p || g->nnz == 0) return TC_OK;
+  TC_TRY(g->erow.alloc((size_t)g->nnz, g->stream));
+  launch(k_erow_rows, grid_for((int64_t)g->n * 32, 256, 16), 256, 0, g->stream, g->off, g->n,
+         g->erow.p);
+  if (g->nlchunks > 0)
+    launch(k_erow_long, (int)std::min<int64_t>(g->nlchunks, (int64_t)sm_count() * 8), kChunk, 0,
+           g->stream, g->off, g->lchunks.p, g->nlchunks, g->erow.p);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 int graph_ingest_checks(tc_graph* g, uint32_t flags) {
   const int T = 256;
   launch(k_ctrl_reset, 1, 32, 0, g->stream, g->ctrl.p);
@@ -208,15 +288,14 @@ int graph_ingest_checks(tc_graph* g, uint32_t flags) {
   TC_TRY(read_ctrl(g));
   if (g->ctrl_host[kCtrlErr]) return describe_err(g, g->ctrl_host[kCtrlErr]);
 
-  TC_TRY(g->erow.alloc((size_t)g->nnz, g->stream));
   // at most nnz / kChunk full chunks plus one partial chunk per long row
   TC_TRY(g->lchunks.alloc((size_t)(g->nnz / kChunk + g->nnz / kLongRow + 1), g->stream));
   if (g->n > 0) {
     const int strict = (flags & TC_GRAPH_VALIDATE) ? 1 : 0;
     launch(k_rows_and_check, grid_for((int64_t)g->n * 32, T, 16), T, 0, g->stream, g->off, g->cols,
-           g->n, g->erow.p, strict, g->lchunks.p, g->ctrl.p);
-    launch(k_rows_long, sm_count() * 2, kChunk, 0, g->stream, g->off, g->cols, g->n, g->erow.p,
-           strict, g->lchunks.p, g->ctrl.p);
+           g->n, strict, g->lchunks.p, g->ctrl.p);
+    launch(k_rows_long, sm_count() * 2, kChunk, 0, g->stream, g->off, g->cols, g->n, strict,
+           g->lchunks.p, g->ctrl.p);
     TC_CUDA(cudaGetLastError());
   }
   if ((flags & TC_GRAPH_CHECK_SYM) && g->nnz > 0) {
@@ -224,6 +303,8 @@ int graph_ingest_checks(tc_graph* g, uint32_t flags) {
     // are known to be in range, so check that first.
     TC_TRY(read_ctrl(g));
     if (g->ctrl_host[kCtrlErr]) return describe_err(g, g->ctrl_host[kCtrlErr]);
+    g->nlchunks = (int64_t)g->ctrl_host[kCtrlLong];
+    TC_TRY(ensure_erow(g));
     launch(k_check_symmetric, grid_for(g->nnz, T), T, 0, g->stream, g->off, g->cols, g->erow.p,
                                                                   g->nnz, g->ctrl.p);
     TC_CUDA(cudaGetLastError());

@@ -122,7 +122,7 @@ struct tc_graph {
   const uint32_t* cols = nullptr;
   tc::DevBuf<int64_t> off_own;
   tc::DevBuf<uint32_t> cols_own;
-  tc::DevBuf<uint32_t> erow;  // row id of every CSR entry (COO rows)
+  tc::DevBuf<uint32_t> erow;  // row id of every CSR entry (COO rows), built on first use
   tc::DevBuf<uint2> lchunks;  // chunks of the rows longer than kLongRow
   int64_t nlchunks = 0;
 
@@ -181,6 +181,7 @@ enum : unsigned long long {
 };
 
 // stage functions (each returns TC_OK or an error)
+int ensure_erow(tc_graph* g);  // COO row ids (graph.cu), built on first use
 int compute_levels(tc_graph* g, const uint32_t* roots_host, uint32_t nroots);
 int compute_segments(tc_graph* g);
 int compute_cover(tc_graph* g);

@@ -338,6 +338,7 @@ int count_plain(tc_graph* g, uint64_t* total, uint32_t* per_entry, int64_t first
   const bool hashed = !merge_only && g->nnz < (int64_t)0xFFFFFFFFll;
   if (per_entry && !hashed)
     return fail(TC_ERR_CAPACITY, "per-entry plain counts need nnz < 2^32");
+  TC_TRY(ensure_erow(g));
   DevBuf<int64_t> ustart;
   if (last > first) {
     if (per_entry)

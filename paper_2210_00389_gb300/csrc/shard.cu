@@ -112,6 +112,7 @@ int shard_bounds(tc_graph* g, int mode, int32_t P, int64_t* bounds_host) {
     if (g->num_cover < 0) TC_TRY(compute_cover(g));
     nidx = g->num_cover;
   } else {
+    TC_TRY(ensure_erow(g));
     nidx = g->nnz;
   }
   const int64_t nch = (nidx + kShardChunk - 1) / kShardChunk;

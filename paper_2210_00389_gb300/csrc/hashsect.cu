@@ -584,13 +584,17 @@ constexpr uint32_t kBatchMaxWork = 64;  // tasks with fewer lookups share a warp
 // Tasks with fewer than kBatchMaxWork lookups are laid end to end in one
 // index space; each lane finds the task of its position by bisection over
 // the warp's inclusive prefix sums (shuffles) and looks the element up.
-// Larger tasks are then done one at a time by the whole warp.
+// Larger tasks are then done one at a time by the whole warp.  Counts only
+// (no per-edge or per-vertex output).
 __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pcols,
                                                 const uint4* __restrict__ descs, uint64_t t0,
                                                 uint32_t nt, const uint32_t* tab, uint32_t nh,
                                                 unsigned long long* probes) {
   const int lane = threadIdx.x & 31;
-  const uint4 ds = (uint32_t)lane < nt ? descs[t0 + lane] : make_uint4(0u, 0u, 0u, 0u);
+  uint4 ds = (uint32_t)lane < nt ? descs[t0 + lane] : make_uint4(0u, 0u, 0u, 0u);
+  // a level-1 cover edge's shared root: one, counted by its lane
+  unsigned c = (ds.y & kRootBonus) ? 1u : 0u;
+  ds.y &= ~kRootBonus;
   const uint32_t w = desc_work(ds);
   const bool small = w < kBatchMaxWork;
   uint32_t s = small ? w : 0u;  // inclusive prefix of the small tasks' work
@@ -602,7 +606,6 @@ __device__ __forceinline__ unsigned probe_batch(const uint32_t* __restrict__ pco
   const uint32_t total = __shfl_sync(0xFFFFFFFFu, s, 31);
   const uint32_t excl = s - (small ? w : 0u);
   const uint32_t xr = ds.y, shift2 = ds.z - ds.y;
-  unsigned c = 0;
   for (uint32_t k0 = 0; k0 < total; k0 += 32 * kUnroll) {
     uint32_t e[kUnroll];
 #pragma unroll

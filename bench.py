@@ -2,8 +2,9 @@
 """Benchmark of the cover-edge triangle count (CETC) on GB300.
 
 One step = one pass of the whole cover-edge path over one graph resident in
-HBM: graph ingest (checks, COO rows, max-degree root), BFS levels, cover-edge
-extraction, intersection with the count-once rule, reduction to a uint64.
+HBM: graph ingest (checks, long-row chunks, max-degree root), BFS levels,
+cover-edge extraction, intersection with the count-once rule, reduction to a
+uint64.
 Workload (default): R-MAT scale 22, edgefactor 16, Graph500 a/b/c/d,
 edge seed 2, relabelled (Fisher-Yates stream 2 + 2^32), symmetrised and
 de-duplicated.  Metric: undirected edges |E| / step time (edges/s).

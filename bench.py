@@ -581,8 +581,9 @@ def run_ours(args, world, rank, local):
     stp = res_plain[0][1]
     ms_kp = statistics.mean(r[1]["ms_main_kernel"] for r in res_plain)
     plain_bytes = float(4 * stp["list_elems"] + 72 * g.num_edges)
-    # the committed DRAM capture is of the R-MAT scale 22 step only
-    tr = ncu_traffic("k_hash_intersect<cover>") if args.workload == "rmat22" else None
+    # the committed DRAM captures are per workload (R-MAT scale 22 and 26)
+    tr = ncu_traffic("k_hash_intersect<cover>" +
+                     ("" if args.workload == "rmat22" else "|" + args.workload))
     stages = {k: statistics.mean(r[1][k] for r in res_cover)
               for k in ("ms_bfs", "ms_cover", "ms_bucket", "ms_intersect", "ms_main_kernel", "ms_total")}
     stages_plain = {"ms_intersect": ms_kp,

@@ -106,6 +106,29 @@ def test_long_rows(tc, name):
     check_graph(tc, g)
 
 
+def _triangle_strip(k):
+    """Vertices 0..k-1 with edges (i, i+1) and (i, i+2): k - 2 triangles in a
+    row, about k / 2 BFS levels deep from an end vertex."""
+    i = np.arange(k, dtype=np.int64)
+    src = np.concatenate([i[:-1], i[:-2]])
+    dst = np.concatenate([i[1:], i[2:]])
+    return gg.from_edges(k, src, dst, name=f"strip{k}")
+
+
+def test_byte_levels_deep_bfs(tc):
+    """Above 2^23 vertices the segmentation reads the levels modulo 256 from
+    a byte copy.  A triangle strip of 1,200 vertices (its component is rooted
+    at its lowest id, so its levels run to 600 and the byte levels wrap
+    twice), a hub-rich R-MAT and enough isolated vertices to pass 2^23:
+    levels, H, every per-edge count and T against the oracle."""
+    g = gg.disjoint_union(_triangle_strip(1200), gg.rmat(12, 16, seed=8),
+                          gg.empty((1 << 23) + 5))
+    assert g.n > (1 << 23)
+    L, nl = oracle.bfs_levels(g)
+    assert int(L[:1200].max()) >= 512
+    check_graph(tc, g)
+
+
 def test_erdos_renyi_and_unions(tc):
     check_graph(tc, gg.erdos_renyi(3000, 0.004, 5))
     check_graph(tc, gg.disjoint_union(gg.rmat(10, 8, seed=3), gg.empty(100),

@@ -73,9 +73,10 @@ size_t csr_bytes(uint32_t n, int64_t nnz) {
   return sizeof(int64_t) * ((size_t)n + 1) + sizeof(uint32_t) * (size_t)nnz;
 }
 
-// Device bytes a one-shot count needs: the CSR, its COO rows, levels, the
-// segmented rows and cover edges, and the bucketing scratch (descriptor,
-// cursor, split and list entries per edge).
+// Device bytes a one-shot count needs (an upper bound for either mode): the
+// CSR, its COO rows (built only by a plain count), levels, the segmented rows
+// and cover edges, and the bucketing scratch (descriptor, cursor, split and
+// list entries per edge).
 size_t one_shot_bytes(uint32_t n, int64_t nnz) {
   return csr_bytes(n, nnz) + (size_t)nnz * (4 + 4 + 4 + 22) + (size_t)n * 80;
 }

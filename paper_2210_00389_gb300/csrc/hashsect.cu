@@ -211,10 +211,10 @@ __device__ __forceinline__ bool owner_hashed(unsigned long long work, uint32_t d
 // Scatter every hashed edge's descriptor (and its index, for per-edge
 // counts) into its owner's task range; edges of owners too light to hash
 // are appended to the merge list.  ostart[o] is the owner's cursor: its
-// first task index, advanced here by one per edge (so it ends at the
-// owner's last task + 1), with bit kLightBit set by k_item_counts for
-// owners too light to hash -- one atomic per owner and warp both places an
-// edge and tells whether it is hashed, with no other per-owner read.
+// first task index, advanced here by one per edge (k_item_write puts it
+// back), with bit kLightBit set by k_item_counts for owners too light to
+// hash -- one atomic per owner and warp both places an edge and tells
+// whether it is hashed, with no other per-owner read.
 constexpr unsigned long long kLightBit = 1ull << 63;
 
 template <int M>
@@ -308,21 +308,25 @@ __global__ void k_item_counts(const int64_t* __restrict__ off, uint32_t n,
   }
 }
 
-// items of class c at items_c[atomic cursor]: (owner, slot << 16 | slots)
+// items of class c at items_c[atomic cursor]: (owner, slot << 16 | slots).
+// Runs after the scatter, which advanced every hashed owner's start by its
+// edge count; the start is put back here.
 __global__ void k_item_write(const int64_t* __restrict__ off, uint32_t n,
                              const uint32_t* __restrict__ owner_cnt,
                              const unsigned long long* __restrict__ owner_work,
                              unsigned long long item_lo, unsigned long long item_hi,
                              unsigned long long item_div, const unsigned long long* ctrl,
                              uint2* __restrict__ items0, uint2* __restrict__ items1,
-                             unsigned long long* cursors) {
+                             unsigned long long* cursors, unsigned long long* __restrict__ ostart) {
   const unsigned long long item_work = item_work_of(ctrl, item_lo, item_hi, item_div);
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; o < (int64_t)n; o += stride) {
     const uint32_t d = degree(off, (uint32_t)o);
-    const uint32_t s = owner_slots(owner_cnt[o], owner_work[o], d, item_work);
+    const uint32_t cnt = owner_cnt[o];
+    const uint32_t s = owner_slots(cnt, owner_work[o], d, item_work);
     if (s == 0) continue;
+    ostart[o] -= cnt;
     const int c = owner_class(d);
     const unsigned long long b = atomicAdd(&cursors[c], (unsigned long long)s);
     uint2* items = c ? items1 : items0;
@@ -673,7 +677,7 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
   for (uint64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const uint2 item = items[it];
     const uint32_t o = item.x, slot = item.y >> 16, nsl = item.y & 0xFFFFu;
-    const uint64_t T = owner_cnt[o], T0 = ostart[o] - T;  // ostart: the scatter's end cursor
+    const uint64_t T0 = ostart[o], T = owner_cnt[o];
     const uint64_t ta = T0 + T * slot / nsl, tb = T0 + T * (slot + 1) / nsl;
     const int64_t ro = off[o];
     const uint32_t d = (uint32_t)(off[o + 1] - ro);
@@ -894,7 +898,8 @@ static int hash_count_mode(tc_graph* g, const EdgeSrc& s, uint64_t nidx, const u
            descs.p, task_split.p, need_idx ? task_idx.p : (uint32_t*)nullptr, small_list.p,
            g->ctrl.p);
     launch(k_item_write, grid_for(g->n, T), T, 0, st, g->off, g->n, owner_cnt.p, owner_work.p,
-           kItemMin[M], kItemMax[M], item_div, g->ctrl.p, items0.p, items1.p, counters.p);
+           kItemMin[M], kItemMax[M], item_div, g->ctrl.p, items0.p, items1.p, counters.p,
+           ostart.p);
   }
   TC_CUDA(cudaGetLastError());
   cudaEventRecord(g->ev[6], st);  // end of bucketing

@@ -31,7 +31,7 @@
 // memory (the CTA's whole table, at most 2/5 full; two independent 4-byte
 // shared loads per lookup) and its warps take the item's edges from a
 // shared counter.
-// Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (five
+// Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (six
 // per SM); larger owners use 1024-thread CTAs with 224 KB tables.  Rows
 // longer than a window (kBigWin entries) are processed in windows of
 // consecutive entries (an id range); every probe run keeps a cursor across
@@ -423,23 +423,6 @@ constexpr int kUnroll = 4;  // probe loads in flight per lane
 
 constexpr uint32_t kGroup = 32 * kUnroll;  // probe elements a warp looks up at once
 
-// A full group: P[lane + 32 j], j < kUnroll, all present, so no bounds or
-// validity tests are executed.
-template <class Sink = NoSink>
-__device__ __forceinline__ unsigned probe_group_full(const uint32_t* __restrict__ P,
-                                                     const uint32_t* tab, uint32_t nh,
-                                                     Sink sink = Sink()) {
-  const int lane = threadIdx.x & 31;
-  uint32_t w[kUnroll];
-  bool ok[kUnroll];
-#pragma unroll
-  for (int j = 0; j < kUnroll; ++j) {
-    w[j] = __ldg(P + j * 32 + lane);
-    ok[j] = true;
-  }
-  return table_find_n<kUnroll>(tab, nh, w, ok, sink);
-}
-
 // U rounds of the remainder index space [0, tt) from k0: element k is
 // R0[k] below s1, R1[k] below s2, else R2[k] (R1, R2 pre-offset).
 template <int U, class Sink = NoSink>
@@ -463,51 +446,52 @@ __device__ __forceinline__ unsigned probe_tail(const uint32_t* __restrict__ R0,
 
 // Look up every element of up to three ranges Q[i][0, m[i]): the full
 // groups of each range without per-element tests, then the ranges'
-// remainders together as one index space, in groups of kUnroll rounds
-// while more than two rounds are left, then one or two rounds (a short
-// remainder does not pay for a whole group).
-template <class Sink = NoSink>
+// remainders together as one index space, in groups of U rounds while
+// more than two rounds are left, then one or two rounds (a short remainder
+// does not pay for a whole group).  U: probe loads per lane and group.
+template <int U = kUnroll, class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_ranges(const uint32_t* Q0, uint32_t m0,
                                                  const uint32_t* Q1, uint32_t m1,
                                                  const uint32_t* Q2, uint32_t m2,
                                                  const uint32_t* tab, uint32_t nh,
                                                  Sink sink = Sink()) {
-  const uint32_t g0 = m0 / kGroup, g1 = m1 / kGroup, g2 = m2 / kGroup;
+  constexpr uint32_t kG = 32u * U;  // elements per group
+  const uint32_t g0 = m0 / kG, g1 = m1 / kG, g2 = m2 / kG;
   const uint32_t g01 = g0 + g1, ng = g01 + g2;
   unsigned c = 0;
   if (ng > 0) {
     const int lane = threadIdx.x & 31;
     auto group_ptr = [&](uint32_t g) {
-      return g < g0 ? Q0 + g * kGroup
-                    : (g < g01 ? Q1 + (g - g0) * kGroup : Q2 + (g - g01) * kGroup);
+      return g < g0 ? Q0 + g * kG
+                    : (g < g01 ? Q1 + (g - g0) * kG : Q2 + (g - g01) * kG);
     };
-    bool ok[kUnroll];
+    bool ok[U];
 #pragma unroll
-    for (int j = 0; j < kUnroll; ++j) ok[j] = true;
-    uint32_t cur[kUnroll], nxt[kUnroll];
+    for (int j = 0; j < U; ++j) ok[j] = true;
+    uint32_t cur[U], nxt[U];
     {
       const uint32_t* gp = group_ptr(0);
 #pragma unroll
-      for (int j = 0; j < kUnroll; ++j) cur[j] = __ldg(gp + j * 32 + lane);
+      for (int j = 0; j < U; ++j) cur[j] = __ldg(gp + j * 32 + lane);
     }
     for (uint32_t g = 1; g < ng; ++g) {
       const uint32_t* gp = group_ptr(g);
 #pragma unroll
-      for (int j = 0; j < kUnroll; ++j) nxt[j] = __ldg(gp + j * 32 + lane);
-      c += table_find_n<kUnroll>(tab, nh, cur, ok, sink);
+      for (int j = 0; j < U; ++j) nxt[j] = __ldg(gp + j * 32 + lane);
+      c += table_find_n<U>(tab, nh, cur, ok, sink);
 #pragma unroll
-      for (int j = 0; j < kUnroll; ++j) cur[j] = nxt[j];
+      for (int j = 0; j < U; ++j) cur[j] = nxt[j];
     }
-    c += table_find_n<kUnroll>(tab, nh, cur, ok, sink);
+    c += table_find_n<U>(tab, nh, cur, ok, sink);
   }
-  const uint32_t f0 = g0 * kGroup, f1 = g1 * kGroup, f2 = g2 * kGroup;
+  const uint32_t f0 = g0 * kG, f1 = g1 * kG, f2 = g2 * kG;
   const uint32_t r0 = m0 - f0, s1 = r0 + (m1 - f1), tt = s1 + (m2 - f2);
   const uint32_t* R0 = Q0 + f0;
   const uint32_t* R1 = Q1 + f1 - r0;
   const uint32_t* R2 = Q2 + f2 - s1;
   uint32_t k0 = 0;
-  for (; k0 + 64 < tt; k0 += kGroup)
-    c += probe_tail<kUnroll>(R0, R1, R2, r0, s1, tt, k0, tab, nh, sink);
+  for (; k0 + 64 < tt; k0 += kG)
+    c += probe_tail<U>(R0, R1, R2, r0, s1, tt, k0, tab, nh, sink);
   if (k0 + 32 < tt) c += probe_tail<2>(R0, R1, R2, r0, s1, tt, k0, tab, nh, sink);
   else if (k0 < tt) c += probe_tail<1>(R0, R1, R2, r0, s1, tt, k0, tab, nh, sink);
   return c;
@@ -529,52 +513,53 @@ __device__ __forceinline__ void prefetch_run_l2(const uint32_t* R, uint32_t len)
 }
 
 // All probe elements of a descriptor: runs [0, x) and [cut, end) of P.
-template <class Sink = NoSink>
+template <int U = kUnroll, class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_all(const uint32_t* __restrict__ P, uint4 ds,
                                               const uint32_t* tab, uint32_t nh,
                                               Sink sink = Sink()) {
-  return probe_ranges(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nh, sink);
+  return probe_ranges<U>(P, ds.y, P + ds.z, ds.w - ds.z, P, 0u, tab, nh, sink);
 }
 
 // This window's part of the sorted run P[a, b) -- its elements <= hi, from
 // a on -- looked up with the window bound checked on the loads the lookups
-// use.  A group of kGroup elements whose last element is inside the run
+// use.  A group of kG elements whose last element is inside the run
 // and <= hi is wholly in the window (the run is sorted) and is looked up
 // without masks; the first group that is not ends the pass, its elements
 // above hi (or past b) masked out, and the set mask bits (a prefix) are
 // the elements it took.  *m = the number of elements looked up.
-template <class Sink = NoSink>
+template <int U = kUnroll, class Sink = NoSink>
 __device__ __forceinline__ unsigned probe_window_run(const uint32_t* __restrict__ P, uint32_t a,
                                                      uint32_t b, uint32_t hi,
                                                      const uint32_t* tab, uint32_t nh,
                                                      uint32_t& m, Sink sink = Sink()) {
+  constexpr uint32_t kG = 32u * U;
   const int lane = threadIdx.x & 31;
   unsigned c = 0;
   uint32_t k = a;
-  bool all[kUnroll];
+  bool all[U];
 #pragma unroll
-  for (int j = 0; j < kUnroll; ++j) all[j] = true;
+  for (int j = 0; j < U; ++j) all[j] = true;
   while (k < b) {
-    uint32_t w[kUnroll];
+    uint32_t w[U];
 #pragma unroll
-    for (int j = 0; j < kUnroll; ++j) {
+    for (int j = 0; j < U; ++j) {
       const uint32_t i = k + j * 32 + lane;
       w[j] = i < b ? __ldg(P + i) : kEmpty;  // kEmpty > hi
     }
-    const uint32_t last = __shfl_sync(0xFFFFFFFFu, w[kUnroll - 1], 31);
+    const uint32_t last = __shfl_sync(0xFFFFFFFFu, w[U - 1], 31);
     if (last <= hi) {  // the whole group: inside the run and the window
-      c += table_find_n<kUnroll>(tab, nh, w, all, sink);
-      k += kGroup;
+      c += table_find_n<U>(tab, nh, w, all, sink);
+      k += kG;
       continue;
     }
-    bool ok[kUnroll];
+    bool ok[U];
     uint32_t cnt = 0;
 #pragma unroll
-    for (int j = 0; j < kUnroll; ++j) {
+    for (int j = 0; j < U; ++j) {
       ok[j] = w[j] <= hi;
       cnt += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, ok[j]));
     }
-    c += table_find_n<kUnroll>(tab, nh, w, ok, sink);
+    c += table_find_n<U>(tab, nh, w, ok, sink);
     k += cnt;
     break;
   }
@@ -583,6 +568,11 @@ __device__ __forceinline__ unsigned probe_window_run(const uint32_t* __restrict_
 }
 
 constexpr uint32_t kBatchMaxWork = 64;  // tasks with fewer lookups share a warp pass
+
+// The medium-owner kernel's block size and probe loads per lane (the large-
+// owner kernel uses kUnroll).
+constexpr int kMedThreadsK = 256;
+constexpr int kMedUnroll = 2;
 
 // Up to 32 tasks t0 .. t0+nt-1 at once: lane j holds task j's descriptor.
 // Tasks with fewer than kBatchMaxWork lookups are laid end to end in one
@@ -664,6 +654,9 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
                  const uint2* __restrict__ H, unsigned long long* __restrict__ tv,
                  unsigned long long* ctrl) {
   constexpr int kWarps = THREADS / 32;
+  // probe loads per lane and group: medium owners' probe runs are a few
+  // hundred elements, so groups of 64 waste fewer lanes in their tails
+  constexpr int U = THREADS == kMedThreadsK ? kMedUnroll : kUnroll;
   constexpr uint32_t kWin = WIN;          // owner entries per table window (at most)
   constexpr uint32_t kHalf = SLOTS / 2;   // slots per half of the two-choice table
   extern __shared__ uint4 tab4[];         // SLOTS slots (dynamic shared memory)
@@ -738,8 +731,8 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
               prefetch_run_l2(P, ds.y);
               prefetch_run_l2(P + ds.z, ds.w - ds.z);
             }
-            if constexpr (VERT) c = probe_all(P, ds, tab, kHalf, ApexSink{tv});
-            else c = probe_all(P, ds, tab, kHalf);
+            if constexpr (VERT) c = probe_all<U>(P, ds, tab, kHalf, ApexSink{tv});
+            else c = probe_all<U>(P, ds, tab, kHalf);
             if (lane == 0) probes += desc_work(ds);
           } else {
             // three sorted runs: [0, x), [cut, z), [z, end), one cursor each
@@ -748,13 +741,13 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
             // this window's elements of each run: the prefix <= hi
             uint32_t m0, m1, m2;
             if constexpr (VERT) {
-              c = probe_window_run(P, cur.x, ds.y, hi, tab, kHalf, m0, ApexSink{tv});
-              c += probe_window_run(P, cur.y, z, hi, tab, kHalf, m1, ApexSink{tv});
-              c += probe_window_run(P, cur.z, ds.w, hi, tab, kHalf, m2, ApexSink{tv});
+              c = probe_window_run<U>(P, cur.x, ds.y, hi, tab, kHalf, m0, ApexSink{tv});
+              c += probe_window_run<U>(P, cur.y, z, hi, tab, kHalf, m1, ApexSink{tv});
+              c += probe_window_run<U>(P, cur.z, ds.w, hi, tab, kHalf, m2, ApexSink{tv});
             } else {
-              c = probe_window_run(P, cur.x, ds.y, hi, tab, kHalf, m0);
-              c += probe_window_run(P, cur.y, z, hi, tab, kHalf, m1);
-              c += probe_window_run(P, cur.z, ds.w, hi, tab, kHalf, m2);
+              c = probe_window_run<U>(P, cur.x, ds.y, hi, tab, kHalf, m0);
+              c += probe_window_run<U>(P, cur.y, z, hi, tab, kHalf, m1);
+              c += probe_window_run<U>(P, cur.z, ds.w, hi, tab, kHalf, m2);
             }
             if (lane == 0) {
               probes += m0 + m1 + m2;
@@ -805,9 +798,10 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
 }
 
 // Table configurations: medium owners (degree <= kMediumMax) in 256-thread
-// CTAs with 32 KB tables (8,192 slots), five per SM; large owners in
-// 1024-thread CTAs with 224 KB tables (57,344 slots), one per SM.
-constexpr int kMedThreads = 256, kMedSlots = 8192, kMedPerSM = 5;
+// CTAs with 32 KB tables (8,192 slots), six per SM (two probe loads per lane
+// keep them at 40 registers); large owners in 1024-thread CTAs with 224 KB
+// tables (57,344 slots), one per SM.
+constexpr int kMedThreads = kMedThreadsK, kMedSlots = 8192, kMedPerSM = 6;
 constexpr int kBigThreads = 1024, kBigSlots = 57344, kBigPerSM = 1;
 // Owner entries per table window, per mode (cover, plain): every owner row
 // longer than this is processed in windows, and each window pass revisits

@@ -31,7 +31,7 @@
 // memory (the CTA's whole table, at most 2/5 full; two independent 4-byte
 // shared loads per lookup) and its warps take the item's edges from a
 // shared counter.
-// Owners of degree <= kMediumMax use 256-thread CTAs with 32 KB tables (six
+// Owners of degree <= kMediumMax use 256-thread CTAs with 28 KB tables (seven
 // per SM); larger owners use 1024-thread CTAs with 224 KB tables.  Rows
 // longer than a window (kBigWin entries) are processed in windows of
 // consecutive entries (an id range); every probe run keeps a cursor across
@@ -798,10 +798,13 @@ k_hash_intersect(const int64_t* __restrict__ off, const uint32_t* __restrict__ c
 }
 
 // Table configurations: medium owners (degree <= kMediumMax) in 256-thread
-// CTAs with 32 KB tables (8,192 slots), six per SM (two probe loads per lane
-// keep them at 40 registers); large owners in 1024-thread CTAs with 224 KB
+// CTAs with 28 KB tables (7,168 slots, at most 2/7 full), seven per SM at 32
+// registers (two probe loads per lane; the plain kernel's batched passes
+// spill 44 bytes there and are still faster); measured faster than five or
+// six per SM with 32 KB tables and than eight with 24 KB at R-MAT scale 22
+// and on Chung-Lu 2^23.  Large owners in 1024-thread CTAs with 224 KB
 // tables (57,344 slots), one per SM.
-constexpr int kMedThreads = kMedThreadsK, kMedSlots = 8192, kMedPerSM = 6;
+constexpr int kMedThreads = kMedThreadsK, kMedSlots = 7168, kMedPerSM = 7;
 constexpr int kBigThreads = 1024, kBigSlots = 57344, kBigPerSM = 1;
 // Owner entries per table window, per mode (cover, plain): every owner row
 // longer than this is processed in windows, and each window pass revisits
